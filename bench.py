@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Benchmark of the RCM ordering hot path on one GB300 (one replica per GPU under torchrun).
+
+Workload: the 192^3 3D 7-point grid with uniformly permuted ids (7,077,888 vertices, 42,246,144
+stored entries, 574 levels per traversal): the high-diameter single-graph case. One step = one
+complete ordering (degree + validation, sorted adjacency, pseudo-peripheral sweeps, labelled
+traversal, reversal) through the C ABI, inputs resident in HBM.
+
+GTEPS = S * m / t, with S the level structures the pseudo-peripheral search computes (Alg. 2;
+2 on this grid, the second one labelled) and m the undirected edges; every implementation of the
+method does these S sweeps, so the rate is proportional to orderings per second.
+
+--impl reference times the serial CPU oracle (the reference arm of this build) on the same
+workload, on the host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SIDE = 192
+METRIC = "RCM GTEPS"
+UNIT = "GTEPS"
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--side", type=int, default=SIDE)
+    p.add_argument("--cpu-samples", type=int, default=3)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def algorithmic_bytes(n: int, nnz: int, levels_only: int, labelled: int) -> int:
+    """Bytes per ordering of the traversal kernel: per levels-only sweep 4(n+1) rowptr + 4nnz
+    colidx + 4nnz neighbour-state gather + 4n level write + 8n queue write/read; a labelled sweep
+    adds 4n degree + 4n parent + 16n key write/read + 4n label."""
+    b_sweep = 4 * (n + 1) + 4 * nnz + 4 * nnz + 4 * n + 8 * n
+    b_lab = b_sweep + 4 * n + 4 * n + 16 * n + 4 * n
+    return levels_only * b_sweep + labelled * b_lab
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_sources_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1610_08128_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, only if the kernel sources still match."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[kernel][workload]
+        if e.get("sources") == kernel_sources_hash():
+            return int(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile(prefix="clocks_", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if gpu_id:
+            cmd += ["-i", gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.out.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.out.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def gpu_uuid(torch):
+    try:
+        u = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+def make_workload(side: int):
+    from paper_1610_08128_gb300 import synth
+
+    g = synth.c2_grid3d(side)
+    return g, {"workload": f"3D 7-point grid {side}^3, ids permuted (seed {g.meta['seed']})",
+               "n": g.n, "nnz": g.nnz}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+
+    g, cfg = make_workload(args.side)
+    m = g.nnz // 2
+    for _ in range(args.warmup):
+        oracle.rcm(g.n, g.rowptr, g.colidx)
+    times, stats = [], None
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        _, stats = oracle.rcm(g.n, g.rowptr, g.colidx, with_stats=True)
+        times.append(time.perf_counter() - t0)
+    t = statistics.mean(times)
+    value = stats["sweeps"] * m / t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} serial orderings of the full workload"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+
+    from paper_1610_08128_gb300 import build as b
+    from paper_1610_08128_gb300 import rcm
+
+    b.build()
+    rcm.load()
+    g, cfg = make_workload(args.side)
+    n, nnz = g.n, g.nnz
+    m = g.offdiag_nnz() // 2
+    rp = torch.from_numpy(g.rowptr).cuda()
+    ci = torch.from_numpy(g.colidx).cuda()
+    perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    opts = rcm.rcm_options()
+    opts.nnz = nnz
+    stream = torch.cuda.current_stream()
+    l2 = torch.cuda.get_device_properties(local).L2_cache_size
+    flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.int32, device="cuda")
+
+    def step(st):
+        s = rcm.rcm_order_ex(n, rp, ci, perm, opts, st, stream)
+        rcm.check(s, "rcm_order_ex")
+
+    for _ in range(args.warmup):
+        step(rcm.rcm_stats())
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(gpu_uuid(torch))
+    step_ms, trav_ms, prep_ms = [], [], []
+    stats = None
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(i)  # L2 flush between steps, outside the timed events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        st = rcm.rcm_stats()
+        e0.record(stream)
+        step(st)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        trav_ms.append(st.traverse_ms)
+        prep_ms.append(st.prep_ms)
+        stats = st.as_dict()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    sweeps = stats["sweeps"]
+    units = sweeps * m * args.steps * world
+    value = units / (total_ms / 1e3) / 1e9
+    ms_per_step = total_ms / args.steps
+
+    # result quality (outside the timed region)
+    bw, prof = rcm.bandwidth_profile(rp, ci, perm)
+
+    # roofline of the dominant kernel: the persistent traversal kernel
+    peak, peak_kind = load_peaks()
+    labelled = 1 if stats["traversals"] == stats["sweeps"] else stats["traversals"] - stats["sweeps"] + 1
+    levels_only = stats["traversals"] - labelled
+    alg = algorithmic_bytes(n, g.offdiag_nnz(), levels_only, labelled)
+    trav = statistics.mean(trav_ms)
+    achieved = alg / (trav / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": recorded_traffic("k_rcm_single", f"grid{args.side}"),
+                "kernel": "k_rcm_single", "kernel_ms": trav, "algorithmic_bytes": alg,
+                "peak_kind": f"{peak_kind} hbm_gbs (copy)"}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hrp = torch.from_numpy(g.rowptr).pin_memory()
+        hci = torch.from_numpy(g.colidx).pin_memory()
+        hpm = torch.empty(n, dtype=torch.int32).pin_memory()
+        rcm.check(rcm.rcm_order_host(n, hrp, hci, hpm, stream), "rcm_order_host")
+        ts = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            rcm.check(rcm.rcm_order_host(n, hrp, hci, hpm, stream), "rcm_order_host")
+            ts.append(time.perf_counter() - t0)
+        assert np.array_equal(hpm.numpy(), perm.cpu().numpy())
+        e2e = {"value": sweeps * m / statistics.mean(ts) / 1e9 * world, "unit": UNIT,
+               "h2d_bytes_per_step": 4 * (n + 1) + 4 * nnz, "d2h_bytes_per_step": 4 * n,
+               "ms_per_step": statistics.mean(ts) * 1e3}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and args.cpu_samples > 0:
+        import oracle
+
+        ts = []
+        for _ in range(args.cpu_samples):
+            t0 = time.perf_counter()
+            oracle.rcm(g.n, g.rowptr, g.colidx)
+            ts.append(time.perf_counter() - t0)
+        cpu = {"value": sweeps * m / statistics.mean(ts) / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_samples} serial orderings of the full workload",
+               "ms_per_ordering": statistics.mean(ts) * 1e3}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": dict(cfg, parallelism="replicas" if world > 1 else "single",
+                           l2="inputs larger than L2, and a 2x-L2 buffer is written between steps"),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 6 * args.steps, "clocks": clocks,
+            "stats": dict(stats, prep_ms=statistics.mean(prep_ms), traverse_ms=trav),
+            "quality": {"bandwidth": bw, "profile": prof},
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,161 @@
+/*
+ * rcm.h -- C ABI of the GB300 (sm_103a) Reverse Cuthill-McKee ordering library.
+ *
+ * Method: Azad, Jacquelin, Buluc, Ng, "The Reverse Cuthill-McKee Algorithm in Distributed-Memory"
+ * (arXiv:1610.08128). The ordering is the one of Sec. II-A / Sec. III with fixed tie rules:
+ *   - D[v] (Alg. 3/4 input) = number of off-diagonal entries in row v; diagonal entries are ignored;
+ *   - components (Sec. III-B: "invoking Alg. 3 for each connected component") are processed in
+ *     start-rule order: each starts at the lowest-id vertex of minimum degree not yet numbered;
+ *   - pseudo-peripheral root (Alg. 2, George-Liu): breadth-first sweeps, each from the lowest-id
+ *     minimum-degree vertex of the previous sweep's last level, while the eccentricity grows
+ *     strictly; the root is the last vertex swept;
+ *   - labelled breadth-first traversal (Alg. 3): each newly reached vertex takes the smallest label
+ *     among its neighbours in the current frontier (SpMSpV over (select2nd, min), Fig. 2); the new
+ *     level is ordered by (parent label, degree, vertex id) (SortPerm, Sec. IV-B) and numbered
+ *     consecutively; labels continue across components;
+ *   - the sequence is reversed once at the end (Alg. 1 last line; Alg. 3 return).
+ *
+ * Conventions shared by every entry point
+ *   Pattern   symmetric sparsity pattern of A in CSR with int32 indices: rowptr[n+1] (rowptr[0] = 0,
+ *             non-decreasing), colidx[rowptr[n]] with 0 <= colidx < n. Values are not passed
+ *             (Sec. III-A: only where the nonzeros are matters). Diagonal entries are allowed and
+ *             ignored. Column order inside a row is free. Duplicate entries are not allowed.
+ *             Symmetry is a precondition and is not checked.
+ *   Output    perm[k] = original vertex placed at new position k (new -> old), so that
+ *             (P A P^T)_{ij} = A_{perm[i], perm[j]}.
+ *   Memory    Pointers documented as "device" must be device-accessible memory of the current
+ *             CUDA device; "host" pointers are ordinary host memory. Inputs stay owned by the
+ *             caller. The library allocates its own workspace (stream-ordered, from the device's
+ *             default memory pool) and frees it in stream order.
+ *   Streams   Device entry points are asynchronous and stream-ordered on `stream` (NULL = legacy
+ *             default stream). Argument errors are returned synchronously. Errors the device
+ *             detects (malformed CSR, a barrier that timed out) are latched per stream and returned
+ *             by rcm_stream_status(). perm is undefined after any error.
+ *   Limits    n < 2^31, nnz = rowptr[n] < 2^31.
+ *   Threads   Entry points may be called from several host threads; calls on different streams
+ *             run independently.
+ */
+#ifndef RCM_GB300_RCM_H
+#define RCM_GB300_RCM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (cudaStream_t). NULL selects the legacy default stream. */
+typedef struct CUstream_st *rcm_stream_t;
+
+typedef enum {
+    RCM_OK = 0,
+    RCM_ERR_INVALID_ARG = 1,    /* bad argument (NULL pointer, negative size, bad options)          */
+    RCM_ERR_BAD_CSR = 2,        /* malformed pattern: rowptr not monotone, colidx out of range     */
+    RCM_ERR_OOM = 3,            /* a device or host allocation failed                              */
+    RCM_ERR_TOO_LARGE = 4,      /* size beyond a documented limit or an admission budget           */
+    RCM_ERR_CUDA = 5,           /* a CUDA runtime call failed                                      */
+    RCM_ERR_TIMEOUT = 6,        /* a bounded device-side wait ran out (grid barrier, queue)        */
+    RCM_ERR_NOT_READY = 7,      /* rcm_poll: the request has not finished                          */
+    RCM_ERR_UNKNOWN_TICKET = 8  /* rcm_poll: no such request                                       */
+} rcm_status;
+
+/* Human-readable name of a status code (static storage). */
+const char *rcm_status_string(rcm_status s);
+
+/* Tuning knobs. None of them changes the result: every setting yields the same permutation.
+   Zero-initialise and set what you need; 0 means "library default" in every field. */
+typedef struct {
+    int32_t narrow_threshold;  /* frontier size below which a single CTA runs the levels; -1 = never */
+    int32_t grid_blocks;       /* CTAs of the persistent grid (<= co-resident limit); 0 = one per SM */
+    int32_t block_threads;     /* threads per CTA of the persistent grid: 256, 512 or 1024; 0 = 1024 */
+    int32_t fused_sweeps;      /* 0/1 = label during sweeps 2.. (fused); -1 = separate labelled pass */
+    int64_t spin_limit_ns;     /* bound of every device-side wait; 0 = 20 s                        */
+    int64_t nnz;               /* rowptr[n] when the caller knows it: skips the synchronised 4-byte
+                                  read (the device still checks it; a mismatch is RCM_ERR_BAD_CSR);
+                                  0 = read it from the device                                       */
+    int32_t debug_stall_barrier; /* test hook: CTA 0 never arrives at the first grid barrier, so
+                                    the others' bounded waits run out and report RCM_ERR_TIMEOUT  */
+    int32_t reserved[3];
+} rcm_options;
+
+/* Statistics of one ordering (filled by rcm_order_ex when requested). */
+typedef struct {
+    int64_t components;      /* connected components                                               */
+    int64_t sweeps;          /* level structures computed by the pseudo-peripheral search (Alg. 2) */
+    int64_t traversals;      /* breadth-first traversals executed (a fused labelled sweep counts once) */
+    int64_t levels;          /* levels expanded over all traversals                                */
+    int64_t max_ecc;         /* largest eccentricity of a root                                     */
+    int64_t isolated;        /* vertices of degree zero                                            */
+    int64_t narrow_levels;   /* levels run by a single CTA                                         */
+    int64_t grid_levels;     /* levels run by the whole persistent grid                            */
+    double prep_ms;          /* device time of the preprocessing kernels (CUDA events)             */
+    double traverse_ms;      /* device time of the persistent traversal kernel (CUDA events)       */
+} rcm_stats;
+
+/*
+ * rcm_order -- RCM permutation of one symmetric pattern (Alg. 2 + Alg. 3, Sec. III).
+ *   n        vertices (rows); 0 is allowed (nothing to do).
+ *   rowptr   device, int32[n+1]; colidx device, int32[rowptr[n]].
+ *   perm_out device, int32[n]; receives perm (new -> old). Also used as the level queue while running.
+ * Reads rowptr[n] from the device once (a 4-byte copy synchronised on `stream`) to size the
+ * workspace, then enqueues all work on `stream` and returns. Device-detected errors: see
+ * rcm_stream_status.
+ */
+rcm_status rcm_order(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t *perm_out,
+                     rcm_stream_t stream);
+
+/*
+ * rcm_order_ex -- rcm_order with options and statistics.
+ *   opts   host, may be NULL (defaults).
+ *   stats  host, may be NULL. When given, the call records CUDA events around its kernels,
+ *          synchronises `stream`, fills *stats, and its return value includes device-detected
+ *          errors (as rcm_stream_status would).
+ */
+rcm_status rcm_order_ex(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t *perm_out,
+                        const rcm_options *opts, rcm_stats *stats, rcm_stream_t stream);
+
+/*
+ * rcm_order_host -- end-to-end ordering from host memory: copies the pattern to the device,
+ * orders it on `stream`, copies perm back, and synchronises. Returns the final status
+ * (device-detected errors included).
+ *   rowptr host int32[n+1], colidx host int32[rowptr[n]], perm_out host int32[n].
+ * Pinned (page-locked) host buffers give the fastest copies; pageable ones work.
+ */
+rcm_status rcm_order_host(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t *perm_out,
+                          rcm_stream_t stream);
+
+/*
+ * rcm_order_batch -- G independent patterns in one call (batched ordering; no counterpart in the
+ * paper, which orders one matrix at a time). The patterns are stacked block-diagonally.
+ *   G        number of graphs (>= 0).
+ *   n_total  total vertices = goff[G] (host value; checked against the device copy).
+ *   goff     device, int64[G+1]: graph g owns global rows goff[g] .. goff[g+1]-1.
+ *   rowptr   device, int32[n_total+1] (global); colidx device, global column ids; every entry of
+ *            graph g's rows must lie inside graph g's block.
+ *   perm_out device, int32[n_total]; segment g receives graph g's perm in LOCAL ids 0..n_g-1, equal
+ *            to rcm_order on that block alone.
+ * Asynchronous on `stream`; device-detected errors as for rcm_order.
+ */
+rcm_status rcm_order_batch(int32_t G, int64_t n_total, const int64_t *goff, const int32_t *rowptr,
+                           const int32_t *colidx, int32_t *perm_out, rcm_stream_t stream);
+
+/* Synchronises `stream` and returns (and clears) the error latched by earlier calls on it. */
+rcm_status rcm_stream_status(rcm_stream_t stream);
+
+/* Workspace bytes rcm_order allocates for a pattern of n vertices and nnz stored entries. */
+size_t rcm_workspace_bytes(int32_t n, int64_t nnz);
+
+/*
+ * rcm_bandwidth_profile -- bandwidth and profile of P A P^T (Sec. II-A): with pos = perm^-1 and
+ * f_i = min(i, min{pos[w] : w adjacent to perm[i]}), beta_i = i - f_i, bandwidth = max beta_i,
+ * profile = |Env| = sum beta_i. All pointers device except bw/profile (host). Synchronous.
+ * Returns RCM_ERR_INVALID_ARG if perm is not a permutation of 0..n-1.
+ */
+rcm_status rcm_bandwidth_profile(int32_t n, const int32_t *rowptr, const int32_t *colidx,
+                                 const int32_t *perm, int64_t *bw, int64_t *profile, rcm_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RCM_GB300_RCM_H */

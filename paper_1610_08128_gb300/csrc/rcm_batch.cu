@@ -1,0 +1,177 @@
+// rcm_batch.cu -- batched ordering: G independent graphs stacked block-diagonally, ordered in one
+// persistent launch. Each CTA pops graphs from a device work queue and runs the whole ordering of
+// a graph with CTA barriers only (Engine<true>), so thousands of small graphs overlap on the GPU
+// with no per-graph launch and no grid-wide barrier. The paper orders one matrix at a time; the
+// batch only multiplies independent instances of the same method, with the same tie rules.
+#include <algorithm>
+#include <mutex>
+
+#include "rcm_engine.cuh"
+#include "rcm_host.hpp"
+#include "rcm_internal.cuh"
+#include "rcm_prep.cuh"
+
+namespace rcm {
+
+// Every stored entry of graph g's rows must stay inside graph g's block, and goff must be a
+// non-decreasing offset array ending at n_total.
+__global__ void k_batch_validate(int G, int n_total, const long long* __restrict__ goff,
+                                 const int* __restrict__ rowptr, const int* __restrict__ colidx, Ctl* ctl) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (goff[0] != 0 || goff[G] != n_total)) atomicOr(&ctl->status, kErrBadCsr);
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x)
+        if (goff[g + 1] < goff[g]) atomicOr(&ctl->status, kErrBadCsr);
+    if (ld_volatile(&ctl->status) & kErrBadCsr) return;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n_total; v += gridDim.x * blockDim.x) {
+        // graph of row v: the last g with goff[g] <= v
+        int lo = 0, hi = G - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (goff[mid] <= v) lo = mid; else hi = mid - 1;
+        }
+        const long long a = goff[lo], b = goff[lo + 1];
+        for (int k = rowptr[v]; k < rowptr[v + 1]; ++k) {
+            const int w = colidx[k];
+            if (w < a || w >= b) atomicOr(&ctl->status, kErrBadCsr);
+        }
+    }
+}
+
+struct BatchArgs {
+    int G;
+    const long long* goff;
+    const int* rowptr;
+    const int* adj;
+    const int* deg;
+    int* claim;
+    int* vis;
+    int* qa;
+    int* qb;
+    int* boff;
+    int* perm;
+    Ctl* ctl;
+};
+
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads) k_rcm_batch(BatchArgs b) {
+    __shared__ int s_scan[33];
+    __shared__ unsigned long long s_min[32];
+    __shared__ int s_bcast[4];
+    __shared__ int s_cnt;
+    __shared__ int s_item;
+    if (ld_volatile(&b.ctl->status) & kErrBadCsr) return;
+    Engine<true> e;
+    while (true) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&b.ctl->work_next, 1);
+        __syncthreads();
+        const int g = s_item;
+        __syncthreads();
+        if (g >= b.G) break;
+        const int v0 = (int)b.goff[g];
+        const int n = (int)(b.goff[g + 1] - b.goff[g]);
+        if (n == 0) continue;
+        EngineArgs a;
+        a.n = n;
+        a.v0 = v0;
+        a.rowptr = b.rowptr;
+        a.adj = b.adj;
+        a.deg = b.deg;
+        a.claim = b.claim;
+        a.vis = b.vis;
+        a.qa = b.qa + v0;
+        a.qb = b.qb + v0;
+        a.boff = b.boff + v0;
+        a.perm = b.perm + v0;
+        a.ctl = b.ctl;
+        a.narrow_thr = 0x7fffffff;
+        a.fused = 1;
+        a.limit_ns = 0;
+        e.init(a, s_scan, s_min, s_bcast, &s_cnt);
+        if (!e.run()) return;
+        __syncthreads();
+        // the segment holds global ids while running; the result is in local ids
+        for (int i = threadIdx.x; i < n; i += kThreads) a.perm[i] -= v0;
+        __syncthreads();
+    }
+}
+
+static std::mutex g_batch_mu;
+static int g_batch_per_sm = -1;
+
+rcm_status order_batch(int32_t G, int64_t n_total, const int64_t* goff, const int32_t* rowptr,
+                       const int32_t* colidx, int32_t* perm, cudaStream_t s) {
+    constexpr int kThreads = 256;
+    const DeviceInfo& di = device_info();
+    {
+        std::lock_guard<std::mutex> g(g_batch_mu);
+        if (g_batch_per_sm < 0) {
+            int bps = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_rcm_batch<kThreads>, kThreads, 0);
+            g_batch_per_sm = bps;
+            cudaFuncSetAttribute(k_sort_rows_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(unsigned long long) * kBigRowSmem));
+        }
+    }
+    if (g_batch_per_sm <= 0) return RCM_ERR_CUDA;
+    // nnz is needed to size the sorted-adjacency copy: one 4-byte read, synchronised on s
+    int nnz = 0;
+    cudaError_t e = cudaMemcpyAsync(&nnz, rowptr + n_total, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (nnz < 0) return RCM_ERR_BAD_CSR;
+    const long long N = std::max<long long>(n_total, 1);
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes, 256);
+        return at;
+    };
+    const size_t o_ctl = take(sizeof(Ctl));
+    const size_t o_pool = take(sizeof(int) * 4 * (size_t)N);
+    const size_t o_deg = take(sizeof(int) * (size_t)N);
+    const size_t o_claim = take(sizeof(int) * (size_t)N);
+    const size_t o_vis = take(sizeof(int) * (size_t)N);
+    const size_t o_big = take(sizeof(int) * (size_t)N);
+    const size_t o_adj = take(sizeof(int) * (size_t)std::max(nnz, 1));
+    void* ws = nullptr;
+    rcm_status st = ws_alloc(&ws, o, s);
+    if (st != RCM_OK) return st;
+    char* base = (char*)ws;
+    Ctl* ctl = (Ctl*)(base + o_ctl);
+    int* pool4 = (int*)(base + o_pool);
+    int* deg = (int*)(base + o_deg);
+    int* claim = (int*)(base + o_claim);
+    int* vis = (int*)(base + o_vis);
+    int* big = (int*)(base + o_big);
+    int* adj = (int*)(base + o_adj);
+    e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), s);
+    if (e == cudaSuccess) {
+        const int pb = 256;
+        const int pgrid = (int)std::max<long long>(1, std::min<long long>((n_total + pb - 1) / pb, (long long)di.sms * 16));
+        k_batch_validate<<<pgrid, pb, 0, s>>>(G, (int)n_total, (const long long*)goff, rowptr, colidx, ctl);
+        k_degree_validate<<<pgrid, pb, 0, s>>>((int)n_total, rowptr, colidx, deg, claim, vis, big, ctl, kSmallRowMax);
+        k_sort_rows_small<<<pgrid, pb, 0, s>>>((int)n_total, rowptr, colidx, deg, adj, ctl);
+        k_sort_rows_big<<<di.sms * 2, 1024, sizeof(unsigned long long) * kBigRowSmem, s>>>(
+            (int)n_total, rowptr, colidx, deg, adj, big, ctl, (unsigned long long*)pool4);
+        BatchArgs b;
+        b.G = G;
+        b.goff = (const long long*)goff;
+        b.rowptr = rowptr;
+        b.adj = adj;
+        b.deg = deg;
+        b.claim = claim;
+        b.vis = vis;
+        b.qa = pool4;
+        b.qb = pool4 + N;
+        b.boff = pool4 + 2 * N;
+        b.perm = perm;
+        b.ctl = ctl;
+        const int blocks = (int)std::min<long long>((long long)g_batch_per_sm * di.sms, std::max(G, 1));
+        k_rcm_batch<kThreads><<<blocks, kThreads, 0, s>>>(b);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = enqueue_latch(ctl, stream_latch(s), nullptr, s);
+    ws_free(ws, s);
+    return e == cudaSuccess ? RCM_OK : cuda_status(e);
+}
+
+}  // namespace rcm

@@ -1,0 +1,173 @@
+// rcm_internal.cuh -- device-side building blocks shared by the library's kernels:
+// the control block, bounded waits, a grid barrier for cooperative launches, and block-level
+// scan/reduce helpers. Everything here is this library's own code (no CUB, no cooperative-groups
+// grid sync), so every wait carries an explicit time limit.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rcm.h"
+
+namespace rcm {
+
+constexpr int kMaxGridBlocks = 2048;
+constexpr int kIntMax = 0x7fffffff;
+constexpr unsigned long long kKeyMax = ~0ull;
+
+// Device-detected error bits (latched into the per-stream status by the host).
+enum : int {
+    kErrBadCsr = 1,     // malformed pattern
+    kErrTimeout = 2,    // a bounded wait ran out
+    kErrInternal = 4,   // an index guard tripped (never expected on valid input)
+    kErrTooLarge = 8,   // a size beyond a fixed capacity
+};
+
+// Control block of one ordering: counters, reduction slots, the grid barrier, and the traversal
+// state that CTA 0 publishes after running narrow levels alone.
+struct alignas(128) Ctl {
+    int status;
+    int maxdeg;
+    int nbig;              // rows longer than the per-thread sorter handles
+    int work_next;         // next work item of a dynamic queue (batched engine)
+    unsigned int bar_arrive;
+    unsigned int bar_gen;
+    int pad1[2];
+    unsigned long long argmin[3];  // ring of min-(degree,id) reduction slots
+    int cnt[3];                    // ring of next-level counters (levels-only sweeps)
+    int pad2;
+    // state published by CTA 0 at the end of a run of narrow levels
+    int pub_F;       // current frontier size (0 = traversal finished)
+    int pub_cur;     // which queue holds the frontier (levels-only sweeps)
+    int pub_ecc;     // levels expanded so far (eccentricity once finished)
+    int pub_start;   // label of the frontier's first vertex (labelled sweeps)
+    int pub_lastF;   // size of the last non-empty level when finished
+    int pub_pad[3];
+    long long stats[8];            // rcm_stats fields, in order
+    int blocksum[kMaxGridBlocks];  // per-CTA totals for grid-wide ordered scans
+};
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
+
+// Coherent (L2) load for data written by other CTAs during this kernel.
+__device__ __forceinline__ int ldcg(const int* p) { return __ldcg(p); }
+
+__device__ __forceinline__ unsigned long long pack_key(int deg, int v) {
+    return ((unsigned long long)(unsigned)deg << 32) | (unsigned)v;
+}
+
+// Bounded grid barrier for a cooperative launch of nblocks CTAs. gen is the CTA's view of the
+// barrier generation (kept in a register by thread 0). Returns false if the barrier failed (a
+// wait ran out or another CTA already reported an error); callers then leave the kernel.
+__device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned nblocks, unsigned& gen,
+                                             long long limit_ns) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned g = gen;
+        __threadfence();
+        unsigned arrived = atomicAdd(&ctl->bar_arrive, 1u);
+        if (arrived == nblocks - 1) {
+            ctl->bar_arrive = 0;
+            __threadfence();
+            atomicExch(&ctl->bar_gen, g + 1);
+        } else {
+            unsigned long long t0 = globaltimer_ns();
+            unsigned spins = 0;
+            while (ld_acquire(&ctl->bar_gen) == g) {
+                if ((++spins & 63u) == 0) {
+                    if (ld_volatile(&ctl->status) & (kErrTimeout | kErrInternal)) { ok = 0; break; }
+                    if ((long long)(globaltimer_ns() - t0) > limit_ns) {
+                        atomicOr(&ctl->status, kErrTimeout);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+        gen = g + 1;
+        if (ok && (ld_volatile(&ctl->status) & (kErrTimeout | kErrInternal))) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ---- block-level helpers (blockDim.x a multiple of 32, at most 1024) ----
+
+__device__ __forceinline__ int warp_incl_scan(int x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Exclusive scan of x over the CTA in thread order; *total receives the sum. Uses 33 ints of smem.
+__device__ __forceinline__ int block_excl_scan(int x, int* total, int* smem) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int incl = warp_incl_scan(x);
+    if (lane == 31) smem[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int v = lane < nw ? smem[lane] : 0;
+        int vi = warp_incl_scan(v);
+        if (lane < nw) smem[lane] = vi - v;
+        if (lane == 31) smem[32] = vi;
+    }
+    __syncthreads();
+    int r = smem[wid] + incl - x;
+    *total = smem[32];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ int block_sum(int x, int* smem) {
+    int t;
+    block_excl_scan(x, &t, smem);
+    return t;
+}
+
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
+        x = y < x ? y : x;
+    }
+    return x;
+}
+
+// Min over the CTA; every thread gets the result. smem: 32 u64.
+__device__ __forceinline__ unsigned long long block_min_u64(unsigned long long x, unsigned long long* smem) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    x = warp_min_u64(x);
+    if (lane == 0) smem[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned long long v = lane < nw ? smem[lane] : kKeyMax;
+        v = warp_min_u64(v);
+        if (lane == 0) smem[0] = v;
+    }
+    __syncthreads();
+    unsigned long long r = smem[0];
+    __syncthreads();
+    return r;
+}
+
+}  // namespace rcm

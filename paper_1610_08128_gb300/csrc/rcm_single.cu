@@ -1,0 +1,150 @@
+// rcm_single.cu -- RCM ordering of one graph: the preprocessing launches (degree + validation,
+// (degree, id)-sorted adjacency) and one cooperative persistent kernel that runs every sweep and
+// every breadth-first level on the device (Engine<false> in rcm_engine.cuh).
+#include <algorithm>
+#include <mutex>
+
+#include "rcm_host.hpp"
+#include "rcm_engine.cuh"
+#include "rcm_internal.cuh"
+#include "rcm_prep.cuh"
+
+namespace rcm {
+
+__global__ void __launch_bounds__(1024, 1) k_rcm_single(EngineArgs args, int stall) {
+    __shared__ int s_scan[33];
+    __shared__ unsigned long long s_min[32];
+    __shared__ int s_bcast[4];
+    __shared__ int s_cnt;
+    if (ld_volatile(&args.ctl->status) & kErrBadCsr) return;
+    if (stall && blockIdx.x == 0) return;  // test hook: the other CTAs' first wait runs out
+    Engine<false> e;
+    e.init(args, s_scan, s_min, s_bcast, &s_cnt);
+    if (e.run() && blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int i = 0; i < 8; ++i) args.ctl->stats[i] = e.st[i];
+    }
+}
+
+// Reduction slots start at the maximum key; the stored-entry count the host sized the workspace
+// for must match rowptr[n] (otherwise the sorted-adjacency copy would not fit).
+__global__ void k_init_ctl(Ctl* ctl, int nnz, const int* rowptr_n) {
+    if (threadIdx.x == 0) {
+        ctl->argmin[0] = ctl->argmin[1] = ctl->argmin[2] = kKeyMax;
+        if (*rowptr_n != nnz) ctl->status |= kErrBadCsr;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// host side
+
+struct SingleLayout {
+    size_t ctl, pool4, deg, claim, vis, bigrows, adj, total;
+};
+
+static SingleLayout single_layout(long long n, long long nnz) {
+    SingleLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes, 256);
+        return at;
+    };
+    L.ctl = take(sizeof(Ctl));
+    L.pool4 = take(sizeof(int) * 4 * (size_t)std::max(n, 1LL));  // qa | qb | boff | spare; sort scratch in prep
+    L.deg = take(sizeof(int) * (size_t)std::max(n, 1LL));
+    L.claim = take(sizeof(int) * (size_t)std::max(n, 1LL));
+    L.vis = take(sizeof(int) * (size_t)std::max(n, 1LL));
+    L.bigrows = take(sizeof(int) * (size_t)std::max(n, 1LL));
+    L.adj = take(sizeof(int) * (size_t)std::max(nnz, 1LL));
+    L.total = o;
+    return L;
+}
+
+static int g_single_blocks_per_sm[4] = {-1, -1, -1, -1};
+static std::mutex g_single_mu;
+
+static int single_blocks_per_sm(int threads) {
+    std::lock_guard<std::mutex> g(g_single_mu);
+    const int idx = threads == 256 ? 0 : threads == 512 ? 1 : 2;
+    if (g_single_blocks_per_sm[idx] < 0) {
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_rcm_single, threads, 0);
+        g_single_blocks_per_sm[idx] = b;
+        cudaFuncSetAttribute(k_sort_rows_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(unsigned long long) * kBigRowSmem));
+    }
+    return g_single_blocks_per_sm[idx];
+}
+
+rcm_status order_single(int32_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colidx,
+                        int32_t* perm, const rcm_options* opts, long long* stats_dev, cudaEvent_t* ev,
+                        cudaStream_t s) {
+    const DeviceInfo& di = device_info();
+    rcm_options o{};
+    if (opts) o = *opts;
+    const int threads = o.block_threads ? o.block_threads : 1024;
+    if (threads != 256 && threads != 512 && threads != 1024) return RCM_ERR_INVALID_ARG;
+    const int per_sm = single_blocks_per_sm(threads);
+    if (per_sm <= 0) return RCM_ERR_CUDA;
+    const int max_blocks = std::min(per_sm * di.sms, kMaxGridBlocks);
+    int blocks = o.grid_blocks ? o.grid_blocks : di.sms;
+    if (blocks < 1 || blocks > max_blocks) return RCM_ERR_INVALID_ARG;
+    int narrow = o.narrow_threshold == 0 ? 2 * threads : (o.narrow_threshold < 0 ? 0 : o.narrow_threshold);
+    const long long limit = o.spin_limit_ns > 0 ? o.spin_limit_ns : 20000000000LL;
+
+    const SingleLayout L = single_layout(n, nnz);
+    void* ws = nullptr;
+    rcm_status st = ws_alloc(&ws, L.total, s);
+    if (st != RCM_OK) return st;
+    char* base = (char*)ws;
+    Ctl* ctl = (Ctl*)(base + L.ctl);
+    int* pool4 = (int*)(base + L.pool4);
+    int* deg = (int*)(base + L.deg);
+    int* claim = (int*)(base + L.claim);
+    int* vis = (int*)(base + L.vis);
+    int* bigrows = (int*)(base + L.bigrows);
+    int* adj = (int*)(base + L.adj);
+
+    cudaError_t e = cudaSuccess;
+    if (ev) e = cudaEventRecord(ev[0], s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), s);
+    if (e == cudaSuccess) {
+        k_init_ctl<<<1, 32, 0, s>>>(ctl, (int)nnz, rowptr + n);
+        const int pb = 256;
+        const int pgrid = (int)std::min<long long>((n + pb - 1) / pb, (long long)di.sms * 16);
+        k_degree_validate<<<std::max(pgrid, 1), pb, 0, s>>>(n, rowptr, colidx, deg, claim, vis, bigrows, ctl,
+                                                           kSmallRowMax);
+        k_sort_rows_small<<<std::max(pgrid, 1), pb, 0, s>>>(n, rowptr, colidx, deg, adj, ctl);
+        k_sort_rows_big<<<di.sms * 2, 1024, sizeof(unsigned long long) * kBigRowSmem, s>>>(
+            n, rowptr, colidx, deg, adj, bigrows, ctl, (unsigned long long*)pool4);
+        e = cudaGetLastError();
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
+    }
+    if (e == cudaSuccess) {
+        EngineArgs args;
+        args.n = n;
+        args.v0 = 0;
+        args.rowptr = rowptr;
+        args.adj = adj;
+        args.deg = deg;
+        args.claim = claim;
+        args.vis = vis;
+        args.qa = pool4;
+        args.qb = pool4 + n;
+        args.boff = pool4 + 2 * (size_t)n;
+        args.perm = perm;
+        args.ctl = ctl;
+        args.narrow_thr = narrow;
+        args.fused = o.fused_sweeps >= 0 ? 1 : 0;
+        args.limit_ns = limit;
+        int stall = o.debug_stall_barrier ? 1 : 0;
+        void* kargs[] = {&args, &stall};
+        e = cudaLaunchCooperativeKernel((const void*)k_rcm_single, dim3(blocks), dim3(threads), kargs, 0, s);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
+    }
+    if (e == cudaSuccess) e = enqueue_latch(ctl, stream_latch(s), stats_dev, s);
+    ws_free(ws, s);
+    return e == cudaSuccess ? RCM_OK : cuda_status(e);
+}
+
+}  // namespace rcm

@@ -1,0 +1,64 @@
+"""The C ABI library builds for sm_103a and exports every entry point include/rcm.h declares.
+
+No compute calls here (no GPU on this host); only pure host functions are called.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1610_08128_gb300 import build as build_mod
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(rcm_\w+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = build_mod.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ("rcm_order", "rcm_order_batch", "rcm_stream_status", "rcm_bandwidth_profile"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_only_functions(lib):
+    from paper_1610_08128_gb300 import rcm
+
+    assert rcm.status_string(0) == "RCM_OK"
+    assert rcm.status_string(6) == "RCM_ERR_TIMEOUT"
+    ws = rcm.rcm_workspace_bytes(4096, 16128)
+    assert ws >= 4 * (8 * 4096 + 16128)
+    assert rcm.rcm_workspace_bytes(-1, 0) == 0
+
+
+def test_binding_refuses_missing_library(monkeypatch, tmp_path):
+    from paper_1610_08128_gb300 import rcm
+
+    monkeypatch.setattr(rcm, "_lib", None)
+    monkeypatch.setattr(rcm, "LIB_PATH", str(tmp_path / "absent.so"))
+    with pytest.raises(RuntimeError):
+        rcm.load()
+
+
+def test_kernels_are_sm103a(lib):
+    """The build targets exactly one architecture: compute_103a -> sm_103a."""
+    assert build_mod.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -1,0 +1,283 @@
+"""GPU parity: the CUDA path (through the C ABI) against the serial CPU oracle, bit for bit.
+
+Orderings are integer permutations, so the only tolerance is exact equality. Inputs are the seeded
+generators' (shapes of the paper's workloads) plus random small graphs, special cases and the
+variant/launch-shape invariance the library promises (no option changes the result).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1610_08128_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1610_08128_gb300 import build, rcm
+
+    build.build()
+    return rcm.load()
+
+
+def rcm_mod():
+    from paper_1610_08128_gb300 import rcm
+
+    return rcm
+
+
+def to_dev(g):
+    rp = torch.from_numpy(np.ascontiguousarray(g.rowptr, dtype=np.int32)).cuda()
+    ci = torch.from_numpy(np.ascontiguousarray(g.colidx if g.nnz else np.zeros(1, np.int32), dtype=np.int32)).cuda()
+    return rp, ci
+
+
+def gpu_perm(g, opts=None, with_stats=False):
+    rcm = rcm_mod()
+    rp, ci = to_dev(g)
+    o = None
+    if opts:
+        o = rcm.rcm_options()
+        for k, v in opts.items():
+            setattr(o, k, v)
+    out = rcm.order(rp, ci, options=o, with_stats=with_stats)
+    if with_stats:
+        return out[0].cpu().numpy(), out[1]
+    return out.cpu().numpy()
+
+
+def assert_parity(g, opts=None):
+    want = oracle.rcm(g.n, g.rowptr, g.colidx)
+    got = gpu_perm(g, opts)
+    assert got.shape == want.shape
+    if not np.array_equal(got, want):
+        bad = np.nonzero(got != want)[0]
+        raise AssertionError(f"mismatch at {len(bad)} positions, first {bad[:8]}: got {got[bad[:8]]} want {want[bad[:8]]}")
+
+
+def small_graphs(count, nmax, seed):
+    rng = synth.rng_for(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.integers(1, nmax + 1))
+        m = int(rng.integers(0, 3 * n + 1))
+        out.append(synth.random_graph(n, m, [seed, i], connected=bool(i % 2), diagonal=bool(i % 3 == 0)))
+    return out
+
+
+# ---------------------------------------------------------------------------------------------
+
+
+def test_c1_grid64_parity():
+    for off in range(4):
+        assert_parity(synth.c1_grid2d(seed_offset=off))
+
+
+def test_random_graphs_fuzz():
+    for g in small_graphs(300, 400, 101):
+        assert_parity(g)
+
+
+def test_grids_2d_3d():
+    for dims, seed in [((1, 1), 1), ((1, 7), 2), ((2, 2), 3), ((13, 29), 4), ((100, 37), 5), ((5, 6, 7), 6),
+                       ((16, 16, 16), 7), ((40, 3, 22), 8), ((64, 64, 8), 9)]:
+        assert_parity(synth.grid(dims, seed=seed))
+
+
+def test_natural_ids_and_paths():
+    for dims in [(10, 10), (3, 50), (4, 5, 6)]:
+        assert_parity(synth.grid(dims))
+    for n in (1, 2, 3, 50, 3000):
+        assert_parity(synth.path(n))
+        assert_parity(synth.path(n, seed=n))
+
+
+def test_trees_and_stars():
+    for i in range(20):
+        assert_parity(synth.random_tree(1 + 37 * i, [5, i]))
+    for leaves in (1, 2, 40, 5000, 20000):  # a row longer than the shared-memory sorter
+        g = synth.csr_from_edges(leaves + 1, np.zeros(leaves, np.int64), np.arange(1, leaves + 1))
+        assert_parity(g)
+
+
+def test_special_cases():
+    rcm = rcm_mod()
+    # n = 0
+    rp = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ci = torch.zeros(1, dtype=torch.int32, device="cuda")
+    pm = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert rcm.rcm_order(0, rp, ci, pm) == rcm.RCM_OK
+    # isolated vertices only, a self-loop only, many components, diagonal everywhere
+    assert_parity(synth.csr_from_edges(1, [], []))
+    assert_parity(synth.csr_from_edges(1, [], [], diagonal=True))
+    assert_parity(synth.csr_from_edges(1000, [], []))
+    assert_parity(synth.csr_from_edges(300, [], [], diagonal=True))
+    assert_parity(synth.random_graph(2000, 700, 7))          # hundreds of components
+    assert_parity(synth.random_graph(2000, 3000, 8, diagonal=np.arange(0, 2000, 7)))
+
+
+def test_meshes():
+    assert_parity(synth.c3_mesh(20000))
+    assert_parity(synth.c3_mesh(20000, seed_offset=1))
+    assert_parity(synth.c3_mesh(8000, stitch=False))          # raw kNN(2): thousands of components
+    assert_parity(synth.knn_mesh(30000, 3, 11))
+
+
+OPTION_SETS = [
+    {"narrow_threshold": -1},            # whole grid for every level
+    {"narrow_threshold": 1 << 30},       # CTA 0 for every level
+    {"narrow_threshold": 7},
+    {"grid_blocks": 1},
+    {"grid_blocks": 3, "narrow_threshold": -1},
+    {"block_threads": 256},
+    {"block_threads": 512, "narrow_threshold": 100},
+    {"fused_sweeps": -1},
+    {"fused_sweeps": -1, "narrow_threshold": -1},
+]
+
+
+@pytest.mark.parametrize("opts", OPTION_SETS, ids=lambda o: ",".join(f"{k}={v}" for k, v in o.items()))
+def test_options_do_not_change_the_result(opts):
+    graphs = [synth.c1_grid2d(), synth.grid((20, 30, 11), seed=3), synth.c3_mesh(6000),
+              synth.random_graph(3000, 4000, 9)] + small_graphs(25, 200, 102)
+    for g in graphs:
+        assert_parity(g, opts)
+
+
+def test_stats_match_oracle():
+    for g in [synth.c1_grid2d(), synth.grid((30, 20, 10), seed=1), synth.c3_mesh(20000)]:
+        _, ost = oracle.rcm(g.n, g.rowptr, g.colidx, with_stats=True)
+        _, st = gpu_perm(g, with_stats=True)
+        assert st["components"] == ost["components"]
+        assert st["sweeps"] == ost["sweeps"]
+        assert st["max_ecc"] == ost["max_ecc"]
+        assert st["traversals"] == ost["sweeps"]   # labelled sweep fused into the last sweep
+
+
+def test_bad_csr_is_reported():
+    rcm = rcm_mod()
+    cases = [
+        (np.array([0, 2, 1, 3], np.int32), np.array([1, 2, 0], np.int32)),   # rowptr decreases
+        (np.array([0, 1, 2, 3], np.int32), np.array([1, 5, 0], np.int32)),   # column out of range
+        (np.array([0, 1, 2, 3], np.int32), np.array([1, -1, 0], np.int32)),  # negative column
+        (np.array([1, 1, 2, 3], np.int32), np.array([1, 0, 0], np.int32)),   # rowptr[0] != 0
+    ]
+    for rp_np, ci_np in cases:
+        rp = torch.from_numpy(rp_np).cuda()
+        ci = torch.from_numpy(ci_np).cuda()
+        pm = torch.empty(3, dtype=torch.int32, device="cuda")
+        st = rcm.rcm_order(3, rp, ci, pm)
+        if st == rcm.RCM_OK:
+            st = rcm.rcm_stream_status()
+        assert st == rcm.RCM_ERR_BAD_CSR
+    # the stream is usable afterwards
+    assert_parity(synth.c1_grid2d())
+
+
+def test_invalid_arguments():
+    rcm = rcm_mod()
+    pm = torch.empty(4, dtype=torch.int32, device="cuda")
+    assert rcm.rcm_order(-1, 0, 0, pm) == rcm.RCM_ERR_INVALID_ARG
+    assert rcm.rcm_order(4, 0, 0, pm) == rcm.RCM_ERR_INVALID_ARG
+    o = rcm.rcm_options()
+    o.block_threads = 300
+    g = synth.c1_grid2d()
+    rp, ci = to_dev(g)
+    perm = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    assert rcm.rcm_order_ex(g.n, rp, ci, perm, o, None) == rcm.RCM_ERR_INVALID_ARG
+    o = rcm.rcm_options()
+    o.grid_blocks = 100000
+    assert rcm.rcm_order_ex(g.n, rp, ci, perm, o, None) == rcm.RCM_ERR_INVALID_ARG
+
+
+def test_bounded_wait_reports_timeout():
+    """CTA 0 never arrives at the first grid barrier (test hook); the other CTAs' bounded waits run
+    out, the kernel returns and the error is reported. Nothing faults or hangs; the context stays usable."""
+    rcm = rcm_mod()
+    g = synth.c1_grid2d()
+    rp, ci = to_dev(g)
+    perm = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    o = rcm.rcm_options()
+    o.debug_stall_barrier = 1
+    o.spin_limit_ns = 200_000_000
+    o.grid_blocks = 4
+    st = rcm.rcm_order_ex(g.n, rp, ci, perm, o, None)
+    if st == rcm.RCM_OK:
+        st = rcm.rcm_stream_status()
+    assert st == rcm.RCM_ERR_TIMEOUT
+    assert_parity(g)
+
+
+def test_bandwidth_profile_matches_oracle():
+    rcm = rcm_mod()
+    for g in [synth.c1_grid2d(), synth.c3_mesh(5000), synth.random_graph(500, 900, 3)]:
+        rp, ci = to_dev(g)
+        for perm in [oracle.rcm(g.n, g.rowptr, g.colidx), np.arange(g.n, dtype=np.int32),
+                     synth.rng_for(1).permutation(g.n).astype(np.int32)]:
+            want = oracle.bandwidth_profile(g.n, g.rowptr, g.colidx, perm)
+            got = rcm.bandwidth_profile(rp, ci, torch.from_numpy(np.ascontiguousarray(perm)).cuda())
+            assert got == want
+        bad = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+        st, _, _ = rcm.rcm_bandwidth_profile(g.n, rp, ci, bad)
+        assert st == rcm.RCM_ERR_INVALID_ARG
+
+
+def test_order_host_end_to_end():
+    rcm = rcm_mod()
+    for g in [synth.c1_grid2d(), synth.c3_mesh(10000), synth.csr_from_edges(5, [], [])]:
+        rp = torch.from_numpy(g.rowptr.copy()).pin_memory()
+        ci = torch.from_numpy(g.colidx.copy() if g.nnz else np.zeros(1, np.int32)).pin_memory()
+        pm = torch.empty(g.n, dtype=torch.int32).pin_memory()
+        rcm.check(rcm.rcm_order_host(g.n, rp, ci, pm), "rcm_order_host")
+        assert np.array_equal(pm.numpy(), oracle.rcm(g.n, g.rowptr, g.colidx))
+
+
+def test_batch_matches_oracle_and_single():
+    rcm = rcm_mod()
+    graphs = [synth.batch_graph(int(k), int(s), [77, i]) for i, (k, s) in
+              enumerate(zip(*synth.mix_sizes(60, 5, 4000, 77)[::-1]))]
+    graphs += [synth.csr_from_edges(1, [], []), synth.csr_from_edges(7, [], []), synth.path(2)]
+    b = synth.concat(graphs)
+    goff = torch.from_numpy(b.goff).cuda()
+    rp = torch.from_numpy(b.rowptr).cuda()
+    ci = torch.from_numpy(b.colidx).cuda()
+    perm = rcm.order_batch(goff, rp, ci).cpu().numpy()
+    for gi, g in enumerate(graphs):
+        seg = perm[b.goff[gi]:b.goff[gi + 1]]
+        want = oracle.rcm(g.n, g.rowptr, g.colidx)
+        assert np.array_equal(seg, want), gi
+        if gi % 10 == 0:
+            assert np.array_equal(seg, gpu_perm(g))
+
+
+def test_batch_rejects_cross_block_entries():
+    rcm = rcm_mod()
+    a, c = synth.path(3), synth.path(3)
+    b = synth.concat([a, c])
+    colidx = b.colidx.copy()
+    colidx[0] = 4  # row 0 of graph 0 points into graph 1
+    goff = torch.from_numpy(b.goff).cuda()
+    rp = torch.from_numpy(b.rowptr).cuda()
+    ci = torch.from_numpy(colidx).cuda()
+    perm = torch.empty(b.n, dtype=torch.int32, device="cuda")
+    st = rcm.rcm_order_batch(2, b.n, goff, rp, ci, perm)
+    if st == rcm.RCM_OK:
+        st = rcm.rcm_stream_status()
+    assert st == rcm.RCM_ERR_BAD_CSR
+
+
+@pytest.mark.slow
+def test_c2_grid192_full_size():
+    """The full 192^3 workload, in the launch configuration the benchmark times."""
+    g = synth.c2_grid3d()
+    assert_parity(g)
+
+
+@pytest.mark.slow
+def test_c3_mesh_full_size():
+    g = synth.c3_mesh()
+    assert_parity(g)
