@@ -68,7 +68,7 @@ const char *rcm_status_string(rcm_status s);
 typedef struct {
     int32_t narrow_threshold;  /* frontier size below which a single CTA runs the levels; -1 = never */
     int32_t grid_blocks;       /* CTAs of the persistent grid (<= co-resident limit); 0 = one per SM */
-    int32_t block_threads;     /* threads per CTA of the persistent grid: 256, 512 or 1024; 0 = 1024 */
+    int32_t block_threads;     /* threads per CTA of the persistent grid: 32 .. 1024 (power of 2); 0 = 512 */
     int32_t fused_sweeps;      /* 0/1 = label during sweeps 2.. (fused); -1 = separate labelled pass */
     int64_t spin_limit_ns;     /* bound of every device-side wait; 0 = 20 s                        */
     int64_t nnz;               /* rowptr[n] when the caller knows it: skips the synchronised 4-byte
@@ -76,7 +76,9 @@ typedef struct {
                                   0 = read it from the device                                       */
     int32_t debug_stall_barrier; /* test hook: CTA 0 never arrives at the first grid barrier, so
                                     the others' bounded waits run out and report RCM_ERR_TIMEOUT  */
-    int32_t reserved[3];
+    int32_t profile_phases;    /* 1 = CTA 0 accumulates %globaltimer time per phase into
+                                  rcm_stats.phase_ns (small overhead)                              */
+    int32_t reserved[2];
 } rcm_options;
 
 /* Statistics of one ordering (filled by rcm_order_ex when requested). */
@@ -91,6 +93,11 @@ typedef struct {
     int64_t grid_levels;     /* levels run by the whole persistent grid                            */
     double prep_ms;          /* device time of the preprocessing kernels (CUDA events)             */
     double traverse_ms;      /* device time of the persistent traversal kernel (CUDA events)       */
+    int64_t phase_ns[8];     /* with profile_phases, CTA 0's time in: [0] levels-only expansion,
+                                [1] labelled claims (phase A), [2] labelled ownership + numbering
+                                (phase B), [3] label writes, [4] grid exchanges, [5] redistribution
+                                exchanges, [6] waiting while CTA 0 runs narrow levels alone,
+                                [7] start-vertex search, isolated vertices and claim resets       */
 } rcm_stats;
 
 /*

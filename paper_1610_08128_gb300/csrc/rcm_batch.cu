@@ -40,9 +40,10 @@ struct BatchArgs {
     int G;
     const long long* goff;
     const int* rowptr;
+    const int4* ell;
     const int* adj;
     const int* deg;
-    int* claim;
+    unsigned long long* claim;
     int* vis;
     int* qa;
     int* qb;
@@ -53,10 +54,7 @@ struct BatchArgs {
 
 template <int kThreads>
 __global__ void __launch_bounds__(kThreads) k_rcm_batch(BatchArgs b) {
-    __shared__ int s_scan[33];
-    __shared__ unsigned long long s_min[32];
-    __shared__ int s_bcast[4];
-    __shared__ int s_cnt;
+    __shared__ EngineSmem smem;
     __shared__ int s_item;
     if (ld_volatile(&b.ctl->status) & kErrBadCsr) return;
     Engine<true> e;
@@ -73,6 +71,7 @@ __global__ void __launch_bounds__(kThreads) k_rcm_batch(BatchArgs b) {
         a.n = n;
         a.v0 = v0;
         a.rowptr = b.rowptr;
+        a.ell = b.ell;
         a.adj = b.adj;
         a.deg = b.deg;
         a.claim = b.claim;
@@ -83,9 +82,12 @@ __global__ void __launch_bounds__(kThreads) k_rcm_batch(BatchArgs b) {
         a.perm = b.perm + v0;
         a.ctl = b.ctl;
         a.narrow_thr = 0x7fffffff;
+        a.obits = claim_order_bits(n);
+        a.profile = 0;
         a.fused = 1;
         a.limit_ns = 0;
-        e.init(a, s_scan, s_min, s_bcast, &s_cnt);
+        __syncthreads();
+        e.init(a, &smem);
         if (!e.run()) return;
         __syncthreads();
         // the segment holds global ids while running; the result is in local ids
@@ -128,10 +130,11 @@ rcm_status order_batch(int32_t G, int64_t n_total, const int64_t* goff, const in
     const size_t o_ctl = take(sizeof(Ctl));
     const size_t o_pool = take(sizeof(int) * 4 * (size_t)N);
     const size_t o_deg = take(sizeof(int) * (size_t)N);
-    const size_t o_claim = take(sizeof(int) * (size_t)N);
+    const size_t o_claim = take(sizeof(unsigned long long) * (size_t)N);
     const size_t o_vis = take(sizeof(int) * (size_t)N);
     const size_t o_big = take(sizeof(int) * (size_t)N);
     const size_t o_adj = take(sizeof(int) * (size_t)std::max(nnz, 1));
+    const size_t o_ell = take(sizeof(int4) * 2 * (size_t)N);
     void* ws = nullptr;
     rcm_status st = ws_alloc(&ws, o, s);
     if (st != RCM_OK) return st;
@@ -139,23 +142,25 @@ rcm_status order_batch(int32_t G, int64_t n_total, const int64_t* goff, const in
     Ctl* ctl = (Ctl*)(base + o_ctl);
     int* pool4 = (int*)(base + o_pool);
     int* deg = (int*)(base + o_deg);
-    int* claim = (int*)(base + o_claim);
+    unsigned long long* claim = (unsigned long long*)(base + o_claim);
     int* vis = (int*)(base + o_vis);
     int* big = (int*)(base + o_big);
     int* adj = (int*)(base + o_adj);
+    int4* ell = (int4*)(base + o_ell);
     e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), s);
     if (e == cudaSuccess) {
         const int pb = 256;
         const int pgrid = (int)std::max<long long>(1, std::min<long long>((n_total + pb - 1) / pb, (long long)di.sms * 16));
         k_batch_validate<<<pgrid, pb, 0, s>>>(G, (int)n_total, (const long long*)goff, rowptr, colidx, ctl);
         k_degree_validate<<<pgrid, pb, 0, s>>>((int)n_total, rowptr, colidx, deg, claim, vis, big, ctl, kSmallRowMax);
-        k_sort_rows_small<<<pgrid, pb, 0, s>>>((int)n_total, rowptr, colidx, deg, adj, ctl);
+        k_sort_rows_small<<<pgrid, pb, 0, s>>>((int)n_total, rowptr, colidx, deg, adj, ell, ctl);
         k_sort_rows_big<<<di.sms * 2, 1024, sizeof(unsigned long long) * kBigRowSmem, s>>>(
-            (int)n_total, rowptr, colidx, deg, adj, big, ctl, (unsigned long long*)pool4);
+            (int)n_total, rowptr, colidx, deg, adj, ell, big, ctl, (unsigned long long*)pool4);
         BatchArgs b;
         b.G = G;
         b.goff = (const long long*)goff;
         b.rowptr = rowptr;
+        b.ell = ell;
         b.adj = adj;
         b.deg = deg;
         b.claim = claim;

@@ -102,8 +102,10 @@ __global__ void k_latch(const Ctl* ctl, int* latch, long long* stats) {
     if (threadIdx.x == 0) {
         const int bits = ((const volatile Ctl*)ctl)->status;
         if (bits && latch) *(volatile int*)latch = *(volatile int*)latch | bits;
-        if (stats)
+        if (stats) {
             for (int i = 0; i < 8; ++i) stats[i] = ctl->stats[i];
+            for (int i = 0; i < 8; ++i) stats[8 + i] = ctl->phase_ns[i];
+        }
     }
 }
 
@@ -137,8 +139,8 @@ static rcm_status check_options(const rcm_options* o) {
     if (!o) return RCM_OK;
     if (o->narrow_threshold < -1 || o->grid_blocks < 0 || o->spin_limit_ns < 0 || o->nnz < 0 || o->nnz >= 0x7fffffffLL)
         return RCM_ERR_INVALID_ARG;
-    if (o->block_threads && o->block_threads != 256 && o->block_threads != 512 && o->block_threads != 1024)
-        return RCM_ERR_INVALID_ARG;
+    const int t = o->block_threads;
+    if (t && t != 32 && t != 64 && t != 128 && t != 256 && t != 512 && t != 1024) return RCM_ERR_INVALID_ARG;
     return RCM_OK;
 }
 
@@ -170,8 +172,12 @@ size_t rcm_workspace_bytes(int32_t n, int64_t nnz) {
     const size_t N = (size_t)std::max(n, 1);
     take(sizeof(Ctl));
     take(sizeof(int) * 4 * N);
-    for (int i = 0; i < 4; ++i) take(sizeof(int) * N);
+    take(sizeof(int) * N);
+    take(sizeof(unsigned long long) * N);
+    take(sizeof(int) * N);
+    take(sizeof(int) * N);
     take(sizeof(int) * (size_t)std::max<int64_t>(nnz, 1));
+    take(sizeof(int) * 8 * N);
     return o;
 }
 
@@ -195,14 +201,14 @@ rcm_status rcm_order_ex(int32_t n, const int32_t* rowptr, const int32_t* colidx,
     long long* stats_dev = nullptr;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     if (stats) {
-        st = ws_alloc((void**)&stats_dev, 8 * sizeof(long long), s);
+        st = ws_alloc((void**)&stats_dev, 16 * sizeof(long long), s);
         if (st != RCM_OK) return st;
-        cudaMemsetAsync(stats_dev, 0, 8 * sizeof(long long), s);
+        cudaMemsetAsync(stats_dev, 0, 16 * sizeof(long long), s);
         for (auto& x : ev) cudaEventCreate(&x);
     }
     st = order_single(n, nnz, rowptr, colidx, perm_out, opts, stats_dev, stats ? ev : nullptr, s);
     if (stats) {
-        long long h[8] = {0};
+        long long h[16] = {0};
         cudaError_t e = cudaMemcpyAsync(h, stats_dev, sizeof(h), cudaMemcpyDeviceToHost, s);
         ws_free(stats_dev, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -223,6 +229,7 @@ rcm_status rcm_order_ex(int32_t n, const int32_t* rowptr, const int32_t* colidx,
         stats->isolated = h[5];
         stats->narrow_levels = h[6];
         stats->grid_levels = h[7];
+        for (int i = 0; i < 8; ++i) stats->phase_ns[i] = h[8 + i];
         if (st == RCM_OK) st = rcm_stream_status(stream);
     }
     return st;

@@ -1,550 +1,934 @@
 // rcm_engine.cuh -- the device-side RCM engine: start vertex, pseudo-peripheral sweeps and the
 // labelled level loop, generic over the executor that runs it.
 //
-//   kCtaOnly = false : one graph, all CTAs of a cooperative persistent grid. Levels with a small
-//                      frontier run on CTA 0 alone (CTA barriers) while the others wait at the next
-//                      grid barrier; wide levels use the whole grid with bounded grid barriers.
+//   kCtaOnly = false : one graph, all CTAs of a cooperative persistent grid. Levels whose frontier
+//                      is small run on CTA 0 alone (CTA barriers, frontier in shared memory) while
+//                      the other CTAs wait at the next exchange; wide levels use the whole grid.
 //   kCtaOnly = true  : one graph per CTA (batched engine); every level uses CTA barriers only.
 //
 // Per component (Sec. III-B: Alg. 3 once per connected component, in start-rule order):
-//   1. start r0 = lowest-id vertex of minimum degree not yet numbered (min-reduction of packed
+//   1. start r0 = lowest-id vertex of minimum degree not yet numbered (min of packed
 //      (degree, id) keys);
 //   2. sweep 1: levels-only BFS from r0 (the level structure of Alg. 2 / the do-while of Alg. 4);
-//      the next root is the min (degree, id) vertex of the last level (REDUCE in Alg. 4);
+//      the next root is the min (degree, id) vertex of the last level (REDUCE in Alg. 4), taken
+//      while that level is expanded;
 //   3. sweeps 2.. (fused mode): labelled BFS (Alg. 3) from the current root. If its eccentricity
 //      does not exceed the previous sweep's, the search stops (loop test of Alg. 2) and the labels
-//      just computed are the final ones, because the root is the last vertex swept. Otherwise the
-//      labels are discarded and the next sweep starts from the last level's min (degree, id).
+//      just computed are final, because the root is the last vertex swept. Otherwise the labels
+//      are discarded and the next sweep starts from the last level's min (degree, id) vertex.
 //      (Separate mode: all sweeps levels-only, then one labelled traversal from the root.)
-// Labelled level (body of Alg. 3), frontier kept in label order:
-//   phase A  SpMSpV over (select2nd, min): each frontier vertex u with label l_u performs
-//            claim[w] = min(claim[w], l_u) on every neighbour. No read of w is needed: vertices
-//            numbered earlier already hold a smaller claim (their parent's label, or their own
-//            label for a root), so the min leaves them unchanged.
-//   phase B  SELECT + SortPerm + "+nv" (Alg. 3): u owns w iff claim[w] == l_u. Rows are pre-sorted
-//            by (degree, id) and the frontier is scanned in label order, so an exclusive prefix sum
-//            of owned-children counts over the frontier gives every child its rank in (parent
-//            label, degree, id) order.
-// The reversal of Alg. 1 is fused: the vertex with label L is written to perm[n-1-L]; the level
-// queues of the labelled sweeps live inside perm.
+//
+// Labelled level d (body of Alg. 3). Every frontier vertex u carries a 64-bit key
+//   key(u) = ((d + 1) << obits) | ord(u),
+// where ord(u) increases with u's label inside the level. Keys therefore increase with the level
+// and, inside a level, follow label order.
+//   phase A  SpMSpV over (select2nd, min): claim[w] = min(claim[w], key(u)) for every neighbour w.
+//            No read of w is needed: a vertex numbered earlier already holds a smaller claim (its
+//            parent's key from an earlier level, or 0 for a root), so the min leaves it unchanged.
+//   phase B  SELECT + SortPerm (Alg. 3): u owns w iff claim[w] == key(u). Rows are pre-sorted by
+//            (degree, id), so scanning the frontier in key order and each row in order lists the
+//            next level in (parent label, degree, id) order; an exclusive prefix sum of
+//            owned-children counts ranks it.
+// On the whole grid, CTA b keeps the children it found as its next slice and numbers them
+// ord = b * slot + j (j = rank inside the CTA), which is already in label order because CTA
+// slices are contiguous in label order. Their final labels ("+nv" of Alg. 3) need the prefix of
+// all CTAs' counts, which the next level's exchange delivers, so a grid level costs one exchange.
+// When slices drift out of balance, or the level becomes small, the level is written to perm at
+// its final labels and redistributed (one more exchange).
+// The reversal of Alg. 1 is fused: the vertex with label L is written to perm[n-1-L].
+//
+// Grid synchronisation is an "exchange": each CTA writes (count, key) into its slot, arrives on a
+// monotone counter with a release reduction, and one thread polls the counter with acquire
+// loads; warp 0 then reads all slots, giving the barrier plus the total, this CTA's prefix, the
+// largest count and the min key. Every wait is bounded by a %globaltimer limit.
 #pragma once
 
 #include "rcm_internal.cuh"
 
 namespace rcm {
 
+constexpr int kEllNb = 7;       // neighbours stored in a vertex's 32-byte row; slot 7 = degree
+constexpr int kCache = 2048;    // frontier ids cached in shared memory per buffer
+constexpr unsigned long long kClaimNone = ~0ull;
+
 struct EngineArgs {
-    int n;                 // vertices of this graph
-    int v0;                // global id of its first vertex (adjacency holds global ids)
-    const int* rowptr;     // global rows
-    const int* adj;        // sorted rows (first deg[v] entries of each row valid)
-    const int* deg;        // global
-    int* claim;            // global
-    int* vis;              // global
-    int* qa;               // this graph's queue (n ints)
-    int* qb;               // this graph's queue (n ints)
-    int* boff;             // this graph's offsets (n ints)
-    int* perm;             // this graph's output segment (n ints); holds global ids while running
+    int n;                       // vertices of this graph
+    int v0;                      // global id of its first vertex (rows hold global ids)
+    const int* rowptr;           // global rows (overflow neighbours of rows with degree > 7)
+    const int4* ell;             // 2 x int4 per vertex: 7 sorted neighbours (-1 padded) + degree
+    const int* adj;              // full sorted rows, valid for rows with degree > 7
+    const int* deg;              // global
+    unsigned long long* claim;   // global, 64-bit keys (kClaimNone = not reached)
+    int* vis;                    // global sweep stamps
+    int* qa;                     // this graph's queue / staging buffer (n ints)
+    int* qb;                     // this graph's queue / staging buffer (n ints)
+    int* boff;                   // this graph's per-frontier offsets (n ints)
+    int* perm;                   // this graph's output segment (n ints); global ids while running
     Ctl* ctl;
     int narrow_thr;
     int fused;
+    int obits;                   // low bits of a key holding the in-level order
+    int profile;                 // accumulate per-phase time (CTA 0, thread 0)
     long long limit_ns;
+};
+
+enum { kPhExpand = 0, kPhClaim, kPhOwn, kPhLabels, kPhExchange, kPhRedist, kPhWaitNarrow, kPhOther };
+
+// Shared memory of one engine CTA.
+struct EngineSmem {
+    EngineArgs args;
+    long long st[8];             // statistics (rcm_stats order), updated by thread 0
+    long long prof[8];           // per-phase ns (profile), updated by thread 0 of CTA 0
+    unsigned long long prof_t;   // timestamp of the last phase boundary
+    int scan[33];
+    int acc_cnt;                 // CTA accumulators feeding the exchange
+    unsigned long long acc_key;
+    int ex[4];                   // exchange results: total, pre, maxcnt
+    unsigned long long ex_key;
+    int bc[8];
+    unsigned long long bck;
+    int tail;
+    int cache[2][kCache];
 };
 
 enum { kStComponents = 0, kStSweeps, kStTraversals, kStLevels, kStMaxEcc, kStIsolated, kStNarrow, kStGrid };
 
+struct ExResult {
+    int total;                // sum of the CTAs' counts
+    int pre;                  // sum over CTAs before this one
+    int maxcnt;               // largest CTA count
+    unsigned long long key;   // min of the CTAs' keys
+};
+
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 template <bool kCtaOnly>
 struct Engine {
-    EngineArgs a;
-    unsigned gen;
+    const EngineArgs* a;   // in shared memory (keeps the per-thread register footprint small)
+    unsigned epoch;
     int sweep_id;
-    int red_k;
-    long long st[8];
-    int* s_scan;                 // 33 ints of shared memory
-    unsigned long long* s_min;   // 32 u64 of shared memory
-    int* s_bcast;                // 4 ints of shared memory
-    int* s_cnt;                  // 1 int of shared memory
+    EngineSmem* sm;
 
-    __device__ void init(const EngineArgs& args, int* scan, unsigned long long* mn, int* bc, int* cnt) {
-        a = args;
-        gen = 0;
-        sweep_id = 0;
-        red_k = 0;
-        for (int i = 0; i < 8; ++i) st[i] = 0;
-        s_scan = scan;
-        s_min = mn;
-        s_bcast = bc;
-        s_cnt = cnt;
-    }
-
-    __device__ bool in_graph(int v) const { return (unsigned)(v - a.v0) < (unsigned)a.n; }
-
-    __device__ bool sync() {
-        if (kCtaOnly) {
-            __syncthreads();
-            return true;
-        }
-        return grid_barrier(a.ctl, gridDim.x, gen, a.limit_ns);
-    }
-
-    __device__ int bcast(const int* p) {
-        if (threadIdx.x == 0) s_bcast[0] = ldcg(p);
-        __syncthreads();
-        int r = s_bcast[0];
-        __syncthreads();
-        return r;
-    }
-
-    __device__ unsigned long long bcast64(const unsigned long long* p) {
+    // All threads call; args are copied to shared memory by thread 0.
+    __device__ void init(const EngineArgs& args, EngineSmem* smem) {
+        sm = smem;
         if (threadIdx.x == 0) {
-            unsigned long long v = __ldcg(p);
-            s_bcast[0] = (int)(unsigned)(v & 0xffffffffu);
-            s_bcast[1] = (int)(unsigned)(v >> 32);
+            smem->args = args;
+            for (int i = 0; i < 8; ++i) smem->st[i] = 0;
+            for (int i = 0; i < 8; ++i) smem->prof[i] = 0;
+            smem->prof_t = globaltimer_ns();
+            smem->acc_cnt = 0;
+            smem->acc_key = kKeyMax;
         }
         __syncthreads();
-        unsigned long long r = ((unsigned long long)(unsigned)s_bcast[1] << 32) | (unsigned)s_bcast[0];
-        __syncthreads();
-        return r;
+        a = &smem->args;
+        epoch = 0;
+        sweep_id = 0;
     }
 
-    __device__ void fail(int bits) { atomicOr(&a.ctl->status, bits); }
+    // Phase boundary: the time since the previous boundary is charged to phase `ph`.
+    __device__ void tick(int ph) {
+        if (a->profile && threadIdx.x == 0 && cta_rank() == 0) {
+            const unsigned long long t = globaltimer_ns();
+            sm->prof[ph] += (long long)(t - sm->prof_t);
+            sm->prof_t = t;
+        }
+    }
 
+    __device__ void stat_add(int i, long long v) {
+        if (threadIdx.x == 0) sm->st[i] += v;
+    }
+    __device__ void stat_max(int i, long long v) {
+        if (threadIdx.x == 0 && v > sm->st[i]) sm->st[i] = v;
+    }
+    __device__ bool in_graph(int v) const { return (unsigned)(v - a->v0) < (unsigned)a->n; }
+    __device__ void fail(int bits) { atomicOr(&a->ctl->status, bits); }
     __device__ int cta_rank() const { return kCtaOnly ? 0 : (int)blockIdx.x; }
     __device__ int cta_count() const { return kCtaOnly ? 1 : (int)gridDim.x; }
 
-    // Min of key(i) over i in [0, count) across the executor; every thread gets the result.
-    template <class KeyF>
-    __device__ bool argmin(int count, KeyF key, unsigned long long& out) {
-        unsigned long long m = kKeyMax;
-        const int stride = cta_count() * blockDim.x;
-        for (int i = cta_rank() * blockDim.x + threadIdx.x; i < count; i += stride) {
-            unsigned long long k = key(i);
-            m = k < m ? k : m;
+    __device__ void load_row(int u, int (&r)[8]) const {
+        const int4* p = a->ell + 2 * (size_t)u;
+        const int4 x = __ldg(p), y = __ldg(p + 1);
+        r[0] = x.x; r[1] = x.y; r[2] = x.z; r[3] = x.w;
+        r[4] = y.x; r[5] = y.y; r[6] = y.z; r[7] = y.w;
+    }
+
+    // Per-thread (count, key) partials into the CTA accumulators (warp-reduced first).
+    __device__ void accumulate(int cnt, unsigned long long key) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            const unsigned long long k = __shfl_xor_sync(0xffffffffu, key, o);
+            key = k < key ? k : key;
         }
-        m = block_min_u64(m, s_min);
+        if ((threadIdx.x & 31) == 0) {
+            if (cnt) atomicAdd(&sm->acc_cnt, cnt);
+            if (key != kKeyMax) atomicMin(&sm->acc_key, key);
+        }
+    }
+
+    // ---- the exchange: grid barrier carrying the accumulated (count, key) of every CTA ----
+    // Callers accumulate() first; the accumulators are consumed and reset. Returns false if a wait
+    // ran out or another CTA failed.
+    __device__ bool exchange(ExResult& r, bool payload = true) {
+        __syncthreads();
         if (kCtaOnly) {
-            out = m;
+            r.total = sm->acc_cnt;
+            r.pre = 0;
+            r.maxcnt = r.total;
+            r.key = sm->acc_key;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                sm->acc_cnt = 0;
+                sm->acc_key = kKeyMax;
+            }
             return true;
         }
-        const int slot = red_k % 3;
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->argmin[(red_k + 1) % 3] = kKeyMax;
-        ++red_k;
-        if (threadIdx.x == 0 && m != kKeyMax) atomicMin(&a.ctl->argmin[slot], m);
-        if (!sync()) return false;
-        out = bcast64(&a.ctl->argmin[slot]);
-        return true;
+        const unsigned e = ++epoch;
+        const int B = gridDim.x, b = blockIdx.x;
+        Ctl* c = a->ctl;
+        if (threadIdx.x < 32) {
+            int bad = 0;
+            if (threadIdx.x == 0) {
+                ExSlot* sl = &c->slots[e & 1][b];
+                sl->flag = ((unsigned long long)e << 32) | (unsigned)sm->acc_cnt;
+                sl->key = sm->acc_key;
+                sm->acc_cnt = 0;
+                sm->acc_key = kKeyMax;
+                red_release_add(&c->arrive, 1u);
+                const unsigned target = e * (unsigned)B;
+                if ((int)(ld_acquire(&c->arrive) - target) < 0) {
+                    const unsigned long long t0 = globaltimer_ns();
+                    unsigned spins = 0;
+                    while ((int)(ld_acquire(&c->arrive) - target) < 0) {
+                        if ((++spins & 31u) == 0) {
+                            if (ld_volatile(&c->status) & (kErrTimeout | kErrInternal)) { bad = 1; break; }
+                            if ((long long)(globaltimer_ns() - t0) > a->limit_ns) {
+                                atomicOr(&c->status, kErrTimeout);
+                                bad = 1;
+                                break;
+                            }
+                        }
+                    }
+                }
+            }
+            bad = __shfl_sync(0xffffffffu, bad, 0);
+            __syncwarp();
+            int x = 0, y = 0, mx = 0;
+            unsigned long long k = kKeyMax;
+            if (payload && !bad) {
+                // slots in batches of 8 per lane: all loads of a batch are issued before use
+                for (int i0 = threadIdx.x; i0 < B; i0 += 32 * 8) {
+                    unsigned long long f[8], kk[8];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        const int i = i0 + 32 * t;
+                        f[t] = i < B ? __ldcg(&c->slots[e & 1][i].flag) : 0ull;
+                        kk[t] = i < B ? __ldcg(&c->slots[e & 1][i].key) : kKeyMax;
+                    }
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        const int i = i0 + 32 * t;
+                        const int v = (int)(unsigned)(f[t] & 0xffffffffu);
+                        if (i < b) x += v;
+                        y += v;
+                        mx = max(mx, v);
+                        k = kk[t] < k ? kk[t] : k;
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    x += __shfl_xor_sync(0xffffffffu, x, o);
+                    y += __shfl_xor_sync(0xffffffffu, y, o);
+                    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                    const unsigned long long kk = __shfl_xor_sync(0xffffffffu, k, o);
+                    k = kk < k ? kk : k;
+                }
+            }
+            if (threadIdx.x == 0) {
+                sm->ex[0] = y;
+                sm->ex[1] = x;
+                sm->ex[2] = mx;
+                sm->ex[3] = bad;
+                sm->ex_key = k;
+            }
+        }
+        __syncthreads();
+        r.total = sm->ex[0];
+        r.pre = sm->ex[1];
+        r.maxcnt = sm->ex[2];
+        r.key = sm->ex_key;
+        const bool ok = sm->ex[3] == 0;
+        __syncthreads();
+        return ok;
     }
 
-    // ---------------- levels-only breadth-first level ----------------
-    // Frontier cur[0..F) in any order, strided from `first` by `stride` (CTA-uniform bounds).
-    // Newly reached vertices get stamp s in vis[] and are appended to nxt through *cnt
-    // (one atomic per warp and neighbour slot).
-    __device__ void expand_levels(int s, const int* cur, int F, int* nxt, int* cnt, int first, int stride) {
-        const int lane = threadIdx.x & 31;
-        for (int i0 = first; i0 < F; i0 += stride) {
-            const int i = i0 + threadIdx.x;
-            int beg = 0, len = 0;
-            if (i < F) {
-                const int u = ldcg(cur + i);
+    __device__ bool barrier() {
+        ExResult r;
+        return exchange(r, false);
+    }
+
+    // ---------------- levels-only level ----------------
+    // Frontier f[i], i in [lo, hi): the shared cache when `cache` is set, else the global queue
+    // cur. Newly reached vertices get stamp s in vis[] and are appended to nxt (positions reserved
+    // once per CTA and round through *tail) and, for positions below kCache, to `ncache`.
+    // Accumulates this CTA's count of new vertices and its min (degree, id) over the slice.
+    __device__ void expand_levels(int s, const int* cur, const int* cache, int lo, int hi, int* nxt,
+                                  int* ncache, int* tail) {
+        const int T = blockDim.x;
+        unsigned long long key = kKeyMax;
+        int cnt = 0;
+        for (int i0 = lo; i0 < hi; i0 += T) {
+            const int i = i0 + (int)threadIdx.x;
+            unsigned mask = 0;
+            int r[8];
+            int d = 0, u = -1;
+            if (i < hi) {
+                u = cache ? cache[i] : ldcg(cur + i);
                 if (!in_graph(u)) {
                     fail(kErrInternal);
+                    u = -1;
                 } else {
-                    beg = __ldg(a.rowptr + u);
-                    len = __ldg(a.deg + u);
+                    load_row(u, r);
+                    d = r[7];
+                    key = min(key, pack_key(d, u));
+                    // issue every exchange before looking at any result, so they overlap
+                    int old[kEllNb];
+#pragma unroll
+                    for (int k = 0; k < kEllNb; ++k) old[k] = k < d ? atomicExch(a->vis + r[k], s) : s;
+#pragma unroll
+                    for (int k = 0; k < kEllNb; ++k) mask |= (old[k] != s ? 1u : 0u) << k;
                 }
             }
-            const int mx = __reduce_max_sync(0xffffffffu, len);
-            for (int k = 0; k < mx; ++k) {
-                bool first_touch = false;
-                int w = 0;
-                if (k < len) {
-                    w = __ldg(a.adj + beg + k);
-                    if (ldcg(a.vis + w) != s) first_touch = atomicExch(a.vis + w, s) != s;
-                }
-                const unsigned m = __ballot_sync(0xffffffffu, first_touch);
-                if (m) {
-                    const int leader = __ffs(m) - 1;
-                    int base = 0;
-                    if (lane == leader) base = atomicAdd(cnt, __popc(m));
-                    base = __shfl_sync(0xffffffffu, base, leader);
-                    if (first_touch) nxt[base + __popc(m & ((1u << lane) - 1u))] = w;
+            // overflow neighbours of rows with degree > 7: appended one by one (rare)
+            if (u >= 0 && d > kEllNb) {
+                const int rp = __ldg(a->rowptr + u);
+                for (int k = kEllNb; k < d; ++k) {
+                    const int w = __ldg(a->adj + rp + k);
+                    if (atomicExch(a->vis + w, s) != s) {
+                        const int pos = atomicAdd(tail, 1);
+                        nxt[pos] = w;
+                        if (ncache && pos < kCache) ncache[pos] = w;
+                        ++cnt;
+                    }
                 }
             }
+            const int c = __popc(mask);
+            int tot;
+            const int ex = block_excl_scan(c, &tot, sm->scan);
+            if (tot) {
+                if (threadIdx.x == 0) sm->bc[0] = atomicAdd(tail, tot);
+                __syncthreads();
+                int pos = sm->bc[0] + ex;
+                __syncthreads();
+#pragma unroll
+                for (int k = 0; k < kEllNb; ++k)
+                    if (mask & (1u << k)) {
+                        nxt[pos] = r[k];
+                        if (ncache && pos < kCache) ncache[pos] = r[k];
+                        ++pos;
+                    }
+            }
+            cnt += c;
         }
+        accumulate(cnt, key);
     }
 
-    // Levels-only sweep from root. On return: ecc, and the last non-empty level lastQ[0..lastF).
-    __device__ bool sweep_levels(int root, int& ecc, const int*& lastQ, int& lastF) {
-        Ctl* c = a.ctl;
+    // Levels-only sweep from root. On return: ecc and the min (degree, id) key of the last level.
+    __device__ bool sweep_levels(int root, int& ecc, unsigned long long& last_key) {
+        Ctl* c = a->ctl;
         const int s = ++sweep_id;
-        if (cta_rank() == 0 && threadIdx.x == 0) {
-            a.vis[root] = s;
-            a.qa[0] = root;
-            if (!kCtaOnly) c->cnt[0] = c->cnt[1] = c->cnt[2] = 0;
+        const int b = cta_rank(), B = cta_count();
+        if (b == 0 && threadIdx.x == 0) {
+            a->vis[root] = s;
+            a->qa[0] = root;
+            sm->cache[0][0] = root;
+            if (!kCtaOnly) c->qtail[0] = c->qtail[1] = c->qtail[2] = 0;
         }
-        if (!sync()) return false;
-        int* cur = a.qa;
-        int* nxt = a.qb;
+        __syncthreads();
+        int* cur = a->qa;
+        int* nxt = a->qb;
         int F = 1;
+        bool in_cache = true;  // CTA 0's shared cache holds the frontier (narrow runs only)
         ecc = 0;
+        if (!kCtaOnly && a->narrow_thr <= 1) {
+            if (!barrier()) return false;
+            in_cache = false;
+        }
+        int cb = 0;
         while (true) {
-            if (kCtaOnly || F < a.narrow_thr) {
-                int last = F;
-                if (kCtaOnly || blockIdx.x == 0) {
-                    while (F > 0 && (kCtaOnly || F < a.narrow_thr)) {
-                        if (threadIdx.x == 0) *s_cnt = 0;
+            if (kCtaOnly || F < a->narrow_thr) {
+                unsigned long long lk = kKeyMax;
+                if (kCtaOnly || b == 0) {
+                    if (!in_cache) {
+                        for (int i = threadIdx.x; i < F; i += blockDim.x) sm->cache[cb][i] = ldcg(cur + i);
+                        in_cache = true;
+                    }
+                    __syncthreads();
+                    while (true) {
+                        if (threadIdx.x == 0) sm->tail = 0;
                         __syncthreads();
-                        expand_levels(s, cur, F, nxt, s_cnt, 0, blockDim.x);
+                        expand_levels(s, cur, F <= kCache ? sm->cache[cb] : nullptr, 0, F, nxt, sm->cache[cb ^ 1],
+                                      &sm->tail);
                         __syncthreads();
-                        const int Fn = *s_cnt;
+                        tick(kPhExpand);
+                        const int cnt = sm->acc_cnt;
+                        const unsigned long long key = sm->acc_key;
                         __syncthreads();
-                        ++st[kStNarrow];
-                        if (Fn == 0) {
-                            last = F;
+                        if (threadIdx.x == 0) {
+                            sm->acc_cnt = 0;
+                            sm->acc_key = kKeyMax;
+                        }
+                        stat_add(kStNarrow, 1);
+                        if (cnt == 0) {
+                            lk = key;
                             F = 0;
                             break;
                         }
                         int* t = cur; cur = nxt; nxt = t;
-                        F = Fn;
+                        cb ^= 1;
+                        F = cnt;
                         ++ecc;
+                        if (!kCtaOnly && F >= a->narrow_thr) break;
                     }
                     if (kCtaOnly) {
-                        lastQ = cur;
-                        lastF = last;
+                        __syncthreads();
+                        last_key = lk;
                         return true;
                     }
                     if (threadIdx.x == 0) {
                         c->pub_F = F;
-                        c->pub_cur = (cur == a.qb) ? 1 : 0;
+                        c->pub_cur = (cur == a->qb) ? 1 : 0;
                         c->pub_ecc = ecc;
-                        c->pub_lastF = last;
-                        c->cnt[ecc % 3] = 0;
+                        c->pub_key = lk;
+                        c->qtail[ecc % 3] = 0;
                     }
                 }
-                if (!sync()) return false;
-                const int Fp = bcast(&c->pub_F);
-                const int pc = bcast(&c->pub_cur);
-                ecc = bcast(&c->pub_ecc);
-                cur = pc ? a.qb : a.qa;
-                nxt = pc ? a.qa : a.qb;
+                tick(kPhOther);
+                if (!barrier()) return false;
+                tick(kPhWaitNarrow);
+                if (threadIdx.x == 0) {
+                    sm->bc[0] = ldcg(&c->pub_F);
+                    sm->bc[1] = ldcg(&c->pub_cur);
+                    sm->bc[2] = ldcg(&c->pub_ecc);
+                    sm->bck = __ldcg(&c->pub_key);
+                }
+                __syncthreads();
+                const int Fp = sm->bc[0], pc = sm->bc[1];
+                ecc = sm->bc[2];
+                lk = sm->bck;
+                __syncthreads();
+                cur = pc ? a->qb : a->qa;
+                nxt = pc ? a->qa : a->qb;
+                in_cache = false;
                 if (Fp == 0) {
-                    lastQ = cur;
-                    lastF = bcast(&c->pub_lastF);
+                    last_key = lk;
                     return true;
                 }
                 F = Fp;
                 continue;
             }
-            int* cnt = &c->cnt[ecc % 3];
-            if (blockIdx.x == 0 && threadIdx.x == 0) c->cnt[(ecc + 1) % 3] = 0;
-            expand_levels(s, cur, F, nxt, cnt, blockIdx.x * blockDim.x, gridDim.x * blockDim.x);
-            if (!sync()) return false;
-            const int Fn = bcast(cnt);
-            ++st[kStGrid];
-            if (Fn == 0) {
-                lastQ = cur;
-                lastF = F;
+            // whole grid: balanced slices of the compact queue
+            int* tail = &c->qtail[ecc % 3];
+            if (b == 0 && threadIdx.x == 0) c->qtail[(ecc + 1) % 3] = 0;
+            const int lo = (int)((long long)F * b / B), hi = (int)((long long)F * (b + 1) / B);
+            expand_levels(s, cur, nullptr, lo, hi, nxt, nullptr, tail);
+            tick(kPhExpand);
+            ExResult r;
+            if (!exchange(r)) return false;
+            tick(kPhExchange);
+            stat_add(kStGrid, 1);
+            if (r.total == 0) {
+                last_key = r.key;
                 return true;
             }
             int* t = cur; cur = nxt; nxt = t;
-            F = Fn;
+            F = r.total;
             ++ecc;
+            in_cache = false;
         }
     }
 
-    // ---------------- labelled level (body of Alg. 3) ----------------
-    // Frontier = labels [start, start+F); the vertex with label L is perm[n-1-L]. On return
-    // total = size of the next level, numbered start+F .. start+F+total-1.
-    template <bool kGrid>
-    __device__ bool labelled_level(int start, int F, int& total) {
-        const int n = a.n;
-        const int next = start + F;
+    // ---------------- labelled sweep (Alg. 3) ----------------
+
+    // A CTA's part of a level: cnt vertex ids, element j at sh[j] (shared memory) or g[step * j]
+    // (global: a staging buffer with step 1, or a label range of perm with step -1).
+    struct Slice {
+        const int* sh;
+        const int* g;
+        int step;
+        int cnt;
+    };
+
+    __device__ int sid(const Slice& s, int j) const { return s.sh ? s.sh[j] : ldcg(s.g + (long long)s.step * j); }
+
+    __device__ Slice perm_range(int first, int cnt) const {
+        Slice s;
+        s.sh = nullptr;
+        s.g = a->perm + (a->n - 1 - first);
+        s.step = -1;
+        s.cnt = cnt;
+        return s;
+    }
+
+    __device__ unsigned long long level_key(int d, unsigned long long ord) const {
+        return ((unsigned long long)(d + 1) << a->obits) | ord;
+    }
+
+    // Bit k set iff the k-th padded-row neighbour is claimed by `key`. All claim loads are issued
+    // before any comparison so that they overlap.
+    __device__ unsigned owned_mask(const int (&rw)[8], int dg, unsigned long long key) const {
+        unsigned long long cl[kEllNb];
+#pragma unroll
+        for (int k = 0; k < kEllNb; ++k) cl[k] = k < dg ? __ldcg(a->claim + rw[k]) : ~key;
+        unsigned mask = 0;
+#pragma unroll
+        for (int k = 0; k < kEllNb; ++k) mask |= (cl[k] == key ? 1u : 0u) << k;
+        return mask;
+    }
+
+    // Phase A over a slice whose element j has key level_key(d, ord0 + j). Accumulates the min
+    // (degree, id) over the slice. The round-0 row stays in (u0, r0) for phase B.
+    __device__ void phase_a(int d, unsigned long long ord0, const Slice& s, int& u0, int (&r0)[8]) {
         const int T = blockDim.x;
-        int lo = 0, hi = F;
-        if (kGrid) {
-            lo = (int)((long long)F * blockIdx.x / gridDim.x);
-            hi = (int)((long long)F * (blockIdx.x + 1) / gridDim.x);
-        }
-        // phase A: claim[w] = min(claim[w], label(u))
-        for (int i = lo + (int)threadIdx.x; i < hi; i += T) {
-            const int u = ldcg(a.perm + (n - 1 - (start + i)));
+        unsigned long long mk = kKeyMax;
+        u0 = -1;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r0[k] = 0;
+        for (int j0 = 0; j0 < s.cnt; j0 += T) {
+            const int j = j0 + (int)threadIdx.x;
+            if (j >= s.cnt) continue;
+            const int u = sid(s, j);
             if (!in_graph(u)) {
                 fail(kErrInternal);
                 continue;
             }
-            const int lu = start + i;
-            const int beg = __ldg(a.rowptr + u), len = __ldg(a.deg + u);
-            for (int k = 0; k < len; ++k) atomicMin(a.claim + __ldg(a.adj + beg + k), lu);
+            int rw[8];
+            load_row(u, rw);
+            const unsigned long long key = level_key(d, ord0 + (unsigned long long)j);
+            const int dg = rw[7];
+#pragma unroll
+            for (int k = 0; k < kEllNb; ++k)
+                if (k < dg) atomicMin(a->claim + rw[k], key);
+            if (dg > kEllNb) {
+                const int rp = __ldg(a->rowptr + u);
+                for (int k = kEllNb; k < dg; ++k) atomicMin(a->claim + __ldg(a->adj + rp + k), key);
+            }
+            mk = min(mk, pack_key(dg, u));
+            if (j0 == 0) {
+                u0 = u;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) r0[k] = rw[k];
+            }
         }
-        if (kGrid) {
-            if (!sync()) return false;
-        } else {
-            __syncthreads();
-        }
-        // phase B1: owned-children counts and CTA-local exclusive offsets in frontier order
-        int carry = 0;
-        for (int i0 = lo; i0 < hi; i0 += T) {
-            const int i = i0 + (int)threadIdx.x;
-            int cnt = 0;
-            if (i < hi) {
-                const int u = ldcg(a.perm + (n - 1 - (start + i)));
+        accumulate(0, mk);
+    }
+
+    // Phase B over the same slice: the children each vertex owns, in key order then row order
+    // (= (parent label, degree, id) order). They go to `ncache` (shared) when this CTA has at most
+    // kCache of them, else to `stage` at positions reserved through *stail; with lab_base >= 0
+    // (single-CTA runs, where final labels are known) also to perm at labels lab_base + rank.
+    // boff_base + j indexes this CTA's per-element offsets (disjoint between CTAs: the label of
+    // element j minus the component's first label, or j in single-CTA runs).
+    // Returns this CTA's child count and, in *out, the slice they form.
+    __device__ int phase_b(int d, unsigned long long ord0, const Slice& s, int u0, const int (&r0)[8],
+                           int* ncache, int* stage, int* stail, int lab_base, int boff_base, Slice* out) {
+        const int T = blockDim.x;
+        const int n = a->n;
+        // pass 1: counts and CTA-local offsets
+        int carry = 0, off0 = 0;
+        unsigned m0 = 0;
+        for (int j0 = 0; j0 < s.cnt; j0 += T) {
+            const int j = j0 + (int)threadIdx.x;
+            int c = 0;
+            unsigned mask = 0;
+            if (j < s.cnt) {
+                int u = u0;
+                int rw[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) rw[k] = r0[k];
+                if (j0 != 0) {
+                    u = sid(s, j);
+                    if (in_graph(u)) load_row(u, rw);
+                }
                 if (in_graph(u)) {
-                    const int lu = start + i;
-                    const int beg = __ldg(a.rowptr + u), len = __ldg(a.deg + u);
-                    for (int k = 0; k < len; ++k) cnt += (ldcg(a.claim + __ldg(a.adj + beg + k)) == lu);
+                    const unsigned long long key = level_key(d, ord0 + (unsigned long long)j);
+                    const int dg = rw[7];
+                    mask = owned_mask(rw, dg, key);
+                    c = __popc(mask);
+                    if (dg > kEllNb) {
+                        const int rp = __ldg(a->rowptr + u);
+                        for (int k = kEllNb; k < dg; ++k) c += (__ldcg(a->claim + __ldg(a->adj + rp + k)) == key);
+                    }
                 }
             }
             int tot;
-            const int ex = block_excl_scan(cnt, &tot, s_scan);
-            if (i < hi) a.boff[i] = carry + ex;
+            const int ex = block_excl_scan(c, &tot, sm->scan);
+            if (j0 == 0) {
+                m0 = mask;
+                off0 = ex;
+            } else if (j < s.cnt) {
+                a->boff[boff_base + j] = carry + ex;
+            }
             carry += tot;
         }
-        int pre = 0;
-        if (kGrid) {
-            if (threadIdx.x == 0) a.ctl->blocksum[blockIdx.x] = carry;
-            if (!sync()) return false;
-            int x = 0, y = 0;
-            for (int b = threadIdx.x; b < (int)gridDim.x; b += T) {
-                const int v = ldcg(a.ctl->blocksum + b);
-                y += v;
-                if (b < (int)blockIdx.x) x += v;
-            }
-            pre = block_sum(x, s_scan);
-            total = block_sum(y, s_scan);
-        } else {
-            total = carry;
+        int* dst = ncache;
+        if (carry > kCache) {
+            if (threadIdx.x == 0) sm->bc[0] = atomicAdd(stail, carry);
+            __syncthreads();
+            dst = stage + sm->bc[0];
+            __syncthreads();
         }
-        // phase B2: children at next + pre + offset, in (parent label, degree, id) order
-        for (int i = lo + (int)threadIdx.x; i < hi; i += T) {
-            const int u = ldcg(a.perm + (n - 1 - (start + i)));
+        out->sh = carry > kCache ? nullptr : ncache;
+        out->g = carry > kCache ? dst : nullptr;
+        out->step = 1;
+        out->cnt = carry;
+        // pass 2: write the children
+        for (int j0 = 0; j0 < s.cnt; j0 += T) {
+            const int j = j0 + (int)threadIdx.x;
+            if (j >= s.cnt) continue;
+            int u = u0;
+            int rw[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) rw[k] = r0[k];
+            unsigned mask = m0;
+            int pos = off0;
+            const unsigned long long key = level_key(d, ord0 + (unsigned long long)j);
+            if (j0 != 0) {
+                u = sid(s, j);
+                if (!in_graph(u)) continue;
+                load_row(u, rw);
+                mask = owned_mask(rw, rw[7], key);
+                pos = a->boff[boff_base + j];
+            }
             if (!in_graph(u)) continue;
-            const int lu = start + i;
-            const int beg = __ldg(a.rowptr + u), len = __ldg(a.deg + u);
-            int lab = next + pre + a.boff[i];
-            for (int k = 0; k < len; ++k) {
-                const int w = __ldg(a.adj + beg + k);
-                if (ldcg(a.claim + w) == lu) {
-                    if ((unsigned)lab < (unsigned)n) {
-                        a.perm[n - 1 - lab] = w;
-                    } else {
-                        fail(kErrInternal);
+#pragma unroll
+            for (int k = 0; k < kEllNb; ++k)
+                if (mask & (1u << k)) {
+                    dst[pos] = rw[k];
+                    if (lab_base >= 0) {
+                        const int lab = lab_base + pos;
+                        if ((unsigned)lab < (unsigned)n) a->perm[n - 1 - lab] = rw[k]; else fail(kErrInternal);
                     }
-                    ++lab;
+                    ++pos;
+                }
+            const int dg = rw[7];
+            if (dg > kEllNb) {
+                const int rp = __ldg(a->rowptr + u);
+                for (int k = kEllNb; k < dg; ++k) {
+                    const int w = __ldg(a->adj + rp + k);
+                    if (__ldcg(a->claim + w) == key) {
+                        dst[pos] = w;
+                        if (lab_base >= 0) {
+                            const int lab = lab_base + pos;
+                            if ((unsigned)lab < (unsigned)n) a->perm[n - 1 - lab] = w; else fail(kErrInternal);
+                        }
+                        ++pos;
+                    }
                 }
             }
         }
-        if (kGrid) {
-            if (!sync()) return false;
-        } else {
-            __syncthreads();
-        }
-        return true;
+        __syncthreads();
+        return carry;
     }
 
-    // Labelled sweep from root, labels from nv. On return: ecc and the last level's label range
-    // [lastStart, lastStart + lastF).
-    __device__ bool sweep_labelled(int root, int nv, int& ecc, int& lastStart, int& lastF) {
-        Ctl* c = a.ctl;
-        if (cta_rank() == 0 && threadIdx.x == 0) {
-            a.claim[root] = nv;
-            a.perm[a.n - 1 - nv] = root;
+    // perm[n-1-(first+j)] = slice element j.
+    __device__ void write_labels(const Slice& s, int first) {
+        const int n = a->n;
+        for (int j = threadIdx.x; j < s.cnt; j += blockDim.x) {
+            const int lab = first + j;
+            const int v = sid(s, j);
+            if ((unsigned)lab < (unsigned)n) a->perm[n - 1 - lab] = v; else fail(kErrInternal);
         }
-        if (kCtaOnly || a.narrow_thr <= 1) {
-            if (!sync()) return false;
+    }
+
+    // Labelled sweep from root, labels from nv. On return: ecc, the min (degree, id) key of the
+    // last level, and the component size (labels nv .. nv+size-1).
+    __device__ bool sweep_labelled(int root, int nv, int& ecc, unsigned long long& last_key, int& size) {
+        Ctl* c = a->ctl;
+        const int b = cta_rank(), B = cta_count();
+        const unsigned long long slot = kCtaOnly ? 0ull : ((1ull << a->obits) - 1ull) / (unsigned long long)B;
+        if (b == 0 && threadIdx.x == 0) {
+            a->claim[root] = 0;
+            a->perm[a->n - 1 - nv] = root;
+            sm->cache[0][0] = root;
+            if (!kCtaOnly) c->qtail[0] = c->qtail[1] = c->qtail[2] = 0;
         }
-        int start = nv, F = 1;
-        ecc = 0;
+        __syncthreads();
+        int d = 0;          // index of the current level
+        int lstart = nv;    // label of its first vertex
+        int cb = 0;         // shared cache buffer holding the current slice (when cached)
+        Slice cur;
+        cur.sh = sm->cache[0];
+        cur.g = nullptr;
+        cur.step = 1;
+        cur.cnt = (b == 0) ? 1 : 0;
+        bool narrow = kCtaOnly || a->narrow_thr > 1;
+        int F = 1;          // level size (known in narrow runs and after redistribution)
+        // the last completed level (grid runs detect the end one level late)
+        int prev_start = nv, prev_size = 1;
+        unsigned long long prev_key = kKeyMax;
         while (true) {
-            if (kCtaOnly || F < a.narrow_thr) {
-                int last = F;
-                if (kCtaOnly || blockIdx.x == 0) {
-                    __syncthreads();
-                    while (F > 0 && (kCtaOnly || F < a.narrow_thr)) {
-                        int total;
-                        labelled_level<false>(start, F, total);
-                        ++st[kStNarrow];
-                        if (total == 0) {
-                            last = F;
+            if (narrow) {
+                unsigned long long lk = kKeyMax;
+                int lastF = 0;
+                if (kCtaOnly || b == 0) {
+                    while (true) {
+                        int u0;
+                        int r0[8];
+                        phase_a(d, 0, cur, u0, r0);
+                        __syncthreads();
+                        tick(kPhClaim);
+                        const unsigned long long key = sm->acc_key;
+                        __syncthreads();
+                        if (threadIdx.x == 0) sm->acc_key = kKeyMax;
+                        if (threadIdx.x == 0) sm->tail = 0;
+                        __syncthreads();
+                        Slice nxt;
+                        int* stage = (d & 1) ? a->qa : a->qb;
+                        const int kids = phase_b(d, 0, cur, u0, r0, sm->cache[cb ^ 1], stage, &sm->tail,
+                                                 lstart + F, 0, &nxt);
+                        tick(kPhOwn);
+                        stat_add(kStNarrow, 1);
+                        if (kids == 0) {
+                            lk = key;
+                            lastF = F;
                             F = 0;
                             break;
                         }
-                        start += F;
-                        F = total;
-                        ++ecc;
+                        lstart += F;
+                        F = kids;
+                        cur = nxt;
+                        cb ^= 1;
+                        ++d;
+                        if (!kCtaOnly && F >= a->narrow_thr) break;
                     }
                     if (kCtaOnly) {
-                        lastStart = start;
-                        lastF = last;
+                        last_key = lk;
+                        ecc = d;
+                        size = lstart + lastF - nv;
                         return true;
                     }
                     if (threadIdx.x == 0) {
                         c->pub_F = F;
-                        c->pub_start = start;
-                        c->pub_ecc = ecc;
-                        c->pub_lastF = last;
+                        c->pub_start = lstart;
+                        c->pub_ecc = d;
+                        c->pub_key = lk;
+                        c->pub_lastF = lastF;
+                        c->qtail[0] = c->qtail[1] = c->qtail[2] = 0;
                     }
                 }
-                if (!sync()) return false;
-                const int Fp = bcast(&c->pub_F);
-                start = bcast(&c->pub_start);
-                ecc = bcast(&c->pub_ecc);
-                if (Fp == 0) {
-                    lastStart = start;
-                    lastF = bcast(&c->pub_lastF);
+                tick(kPhOther);
+                if (!barrier()) return false;
+                tick(kPhWaitNarrow);
+                if (threadIdx.x == 0) {
+                    sm->bc[0] = ldcg(&c->pub_F);
+                    sm->bc[1] = ldcg(&c->pub_start);
+                    sm->bc[2] = ldcg(&c->pub_ecc);
+                    sm->bc[3] = ldcg(&c->pub_lastF);
+                    sm->bck = __ldcg(&c->pub_key);
+                }
+                __syncthreads();
+                F = sm->bc[0];
+                lstart = sm->bc[1];
+                d = sm->bc[2];
+                const int lastF2 = sm->bc[3];
+                lk = sm->bck;
+                __syncthreads();
+                if (F == 0) {
+                    last_key = lk;
+                    ecc = d;
+                    size = lstart + lastF2 - nv;
                     return true;
                 }
-                F = Fp;
+                // whole grid from here: balanced slices of the level's label range in perm
+                const int lo = (int)((long long)F * b / B), hi = (int)((long long)F * (b + 1) / B);
+                cur = perm_range(lstart + lo, hi - lo);
+                narrow = false;
                 continue;
             }
-            int total = 0;
-            if (!labelled_level<true>(start, F, total)) return false;
-            ++st[kStGrid];
-            if (total == 0) {
-                lastStart = start;
-                lastF = F;
+            // ---- whole-grid level d: this CTA's slice, ord = b * slot + j ----
+            const unsigned long long ord0 = (unsigned long long)b * slot;
+            int u0;
+            int r0[8];
+            phase_a(d, ord0, cur, u0, r0);
+            if (threadIdx.x == 0) atomicAdd(&sm->acc_cnt, cur.cnt);
+            tick(kPhClaim);
+            ExResult r;
+            if (!exchange(r)) return false;
+            tick(kPhExchange);
+            stat_add(kStGrid, 1);
+            if (r.total == 0) {
+                last_key = prev_key;
+                ecc = d - 1;
+                size = prev_start + prev_size - nv;
                 return true;
             }
-            start += F;
-            F = total;
-            ++ecc;
+            write_labels(cur, lstart + r.pre);
+            tick(kPhLabels);
+            if (b == 0 && threadIdx.x == 0) c->qtail[(d + 2) % 3] = 0;
+            Slice nxt;
+            int* stage = (d & 1) ? a->qa : a->qb;
+            const int kids = phase_b(d, ord0, cur, u0, r0, sm->cache[cb ^ 1], stage, &c->qtail[(d + 1) % 3], -1,
+                                     lstart + r.pre - nv, &nxt);
+            tick(kPhOwn);
+            prev_start = lstart;
+            prev_size = r.total;
+            prev_key = r.key;
+            lstart += r.total;
+            ++d;
+            cur = nxt;
+            if (cur.sh) cb ^= 1;
+            const int fair = (r.total + B - 1) / B;
+            if (r.total < a->narrow_thr || r.maxcnt > 2 * fair + 64) {
+                // number level d now and redistribute it (or hand it to CTA 0)
+                if (threadIdx.x == 0) atomicAdd(&sm->acc_cnt, kids);
+                ExResult r2;
+                if (!exchange(r2)) return false;
+                if (r2.total == 0) {
+                    last_key = prev_key;
+                    ecc = d - 1;
+                    size = lstart - nv;
+                    return true;
+                }
+                write_labels(cur, lstart + r2.pre);
+                if (!barrier()) return false;
+                tick(kPhRedist);
+                F = r2.total;
+                if (F < a->narrow_thr) {
+                    narrow = true;
+                    cur = perm_range(lstart, b == 0 ? F : 0);
+                    continue;
+                }
+                const int lo = (int)((long long)F * b / B), hi = (int)((long long)F * (b + 1) / B);
+                cur = perm_range(lstart + lo, hi - lo);
+            }
         }
     }
 
-    // Degree-zero vertices are the first components in start-rule order: they take labels
-    // 0..Z-1 in increasing id (an ordered compaction).
+    // Degree-zero vertices are the first components in start-rule order: labels 0..Z-1 in
+    // increasing id (an ordered compaction).
     __device__ bool label_isolated(int& Z) {
-        const int n = a.n;
+        const int n = a->n;
         const int R = cta_rank(), C = cta_count();
         const int lo = (int)((long long)n * R / C);
         const int hi = (int)((long long)n * (R + 1) / C);
         int cnt = 0;
-        for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) cnt += (__ldg(a.deg + a.v0 + i) == 0);
-        cnt = block_sum(cnt, s_scan);
-        int carry = 0;
-        if (kCtaOnly) {
-            Z = cnt;
-        } else {
-            if (threadIdx.x == 0) a.ctl->blocksum[blockIdx.x] = cnt;
-            if (!sync()) return false;
-            int x = 0, y = 0;
-            for (int b = threadIdx.x; b < C; b += blockDim.x) {
-                const int v = ldcg(a.ctl->blocksum + b);
-                y += v;
-                if (b < R) x += v;
-            }
-            carry = block_sum(x, s_scan);
-            Z = block_sum(y, s_scan);
-        }
+        for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) cnt += (__ldg(a->deg + a->v0 + i) == 0);
+        accumulate(cnt, kKeyMax);
+        ExResult r;
+        if (!exchange(r)) return false;
+        Z = r.total;
         if (Z == 0) return true;
+        int carry = r.pre;
         for (int i0 = lo; i0 < hi; i0 += blockDim.x) {
             const int i = i0 + (int)threadIdx.x;
-            const int f = (i < hi && __ldg(a.deg + a.v0 + i) == 0) ? 1 : 0;
+            const int f = (i < hi && __ldg(a->deg + a->v0 + i) == 0) ? 1 : 0;
             int tot;
-            const int ex = block_excl_scan(f, &tot, s_scan);
+            const int ex = block_excl_scan(f, &tot, sm->scan);
             if (f) {
                 const int lab = carry + ex;
-                a.perm[n - 1 - lab] = a.v0 + i;
-                a.claim[a.v0 + i] = lab;
+                a->perm[n - 1 - lab] = a->v0 + i;
+                a->claim[a->v0 + i] = 0;
             }
             carry += tot;
         }
-        return sync();
+        return barrier();
     }
 
     __device__ bool reset_claims(int nv, int size) {
-        const int n = a.n;
+        const int n = a->n;
         const int stride = cta_count() * blockDim.x;
         for (int i = cta_rank() * blockDim.x + threadIdx.x; i < size; i += stride) {
-            const int v = ldcg(a.perm + (n - 1 - (nv + i)));
-            if (in_graph(v)) a.claim[v] = kIntMax;
+            const int v = ldcg(a->perm + (n - 1 - (nv + i)));
+            if (in_graph(v)) a->claim[v] = kClaimNone;
         }
-        return sync();
+        return barrier();
+    }
+
+    // Start of the next component: min (degree, id) over the vertices not yet numbered.
+    __device__ bool next_start(unsigned long long& out) {
+        unsigned long long m = kKeyMax;
+        const int stride = cta_count() * blockDim.x;
+        for (int i = cta_rank() * blockDim.x + threadIdx.x; i < a->n; i += stride) {
+            const int v = a->v0 + i;
+            if (__ldcg(a->claim + v) == kClaimNone) {
+                const unsigned long long k = pack_key(__ldg(a->deg + v), v);
+                m = k < m ? k : m;
+            }
+        }
+        accumulate(0, m);
+        ExResult r;
+        if (!exchange(r)) return false;
+        out = r.key;
+        return true;
     }
 
     // The whole ordering of this graph. Returns false on a failed wait or guard.
     __device__ bool run() {
-        const int n = a.n;
+        const int n = a->n;
         int Z = 0;
         if (!label_isolated(Z)) return false;
-        st[kStIsolated] = Z;
-        st[kStComponents] = Z;
+        stat_add(kStIsolated, Z);
+        stat_add(kStComponents, Z);
         int nv = Z;
-        const int* deg = a.deg;
-        const int* claim = a.claim;
-        const int v0 = a.v0;
         while (nv < n) {
             unsigned long long k0;
-            if (!argmin(n, [&](int i) {
-                    const int v = v0 + i;
-                    return ldcg(claim + v) == kIntMax ? pack_key(__ldg(deg + v), v) : kKeyMax;
-                }, k0))
-                return false;
+            tick(kPhOther);
+            if (!next_start(k0)) return false;
+            tick(kPhOther);
             if (k0 == kKeyMax) {
                 fail(kErrInternal);
                 return false;
             }
-            ++st[kStComponents];
+            stat_add(kStComponents, 1);
             int r = (int)(unsigned)(k0 & 0xffffffffu);
-            int ecc_prev, lastF;
-            const int* lastQ;
-            if (!sweep_levels(r, ecc_prev, lastQ, lastF)) return false;
-            ++st[kStSweeps];
-            ++st[kStTraversals];
-            st[kStLevels] += ecc_prev + 1;
+            int ecc_prev;
             unsigned long long k1;
-            if (!argmin(lastF, [&](int i) {
-                    const int v = ldcg(lastQ + i);
-                    return pack_key(__ldg(deg + v), v);
-                }, k1))
-                return false;
+            if (!sweep_levels(r, ecc_prev, k1)) return false;
+            stat_add(kStSweeps, 1);
+            stat_add(kStTraversals, 1);
+            stat_add(kStLevels, ecc_prev + 1);
             r = (int)(unsigned)(k1 & 0xffffffffu);
             int size = 0, ecc_root = 0;
-            if (a.fused) {
+            if (a->fused) {
                 while (true) {
-                    int ecc, ls, lf;
-                    if (!sweep_labelled(r, nv, ecc, ls, lf)) return false;
-                    ++st[kStSweeps];
-                    ++st[kStTraversals];
-                    st[kStLevels] += ecc + 1;
-                    size = ls + lf - nv;
+                    int ecc;
+                    unsigned long long k2;
+                    if (!sweep_labelled(r, nv, ecc, k2, size)) return false;
+                    stat_add(kStSweeps, 1);
+                    stat_add(kStTraversals, 1);
+                    stat_add(kStLevels, ecc + 1);
                     if (ecc <= ecc_prev) {
                         ecc_root = ecc;
                         break;
                     }
                     ecc_prev = ecc;
-                    unsigned long long k2;
-                    if (!argmin(lf, [&](int i) {
-                            const int v = ldcg(a.perm + (n - 1 - (ls + i)));
-                            return pack_key(__ldg(deg + v), v);
-                        }, k2))
-                        return false;
+                    tick(kPhOther);
                     if (!reset_claims(nv, size)) return false;
+                    tick(kPhOther);
                     r = (int)(unsigned)(k2 & 0xffffffffu);
                 }
             } else {
                 while (true) {
                     int ecc;
-                    if (!sweep_levels(r, ecc, lastQ, lastF)) return false;
-                    ++st[kStSweeps];
-                    ++st[kStTraversals];
-                    st[kStLevels] += ecc + 1;
+                    unsigned long long k2;
+                    if (!sweep_levels(r, ecc, k2)) return false;
+                    stat_add(kStSweeps, 1);
+                    stat_add(kStTraversals, 1);
+                    stat_add(kStLevels, ecc + 1);
                     if (ecc <= ecc_prev) break;
                     ecc_prev = ecc;
-                    unsigned long long k2;
-                    if (!argmin(lastF, [&](int i) {
-                            const int v = ldcg(lastQ + i);
-                            return pack_key(__ldg(deg + v), v);
-                        }, k2))
-                        return false;
                     r = (int)(unsigned)(k2 & 0xffffffffu);
                 }
-                int ls, lf;
-                if (!sweep_labelled(r, nv, ecc_root, ls, lf)) return false;
-                ++st[kStTraversals];
-                st[kStLevels] += ecc_root + 1;
-                size = ls + lf - nv;
+                unsigned long long k2;
+                if (!sweep_labelled(r, nv, ecc_root, k2, size)) return false;
+                stat_add(kStTraversals, 1);
+                stat_add(kStLevels, ecc_root + 1);
             }
-            if (ecc_root > st[kStMaxEcc]) st[kStMaxEcc] = ecc_root;
+            stat_max(kStMaxEcc, ecc_root);
             if (size <= 0) {
                 fail(kErrInternal);
                 return false;

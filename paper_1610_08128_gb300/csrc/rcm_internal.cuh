@@ -1,7 +1,7 @@
-// rcm_internal.cuh -- device-side building blocks shared by the library's kernels:
-// the control block, bounded waits, a grid barrier for cooperative launches, and block-level
-// scan/reduce helpers. Everything here is this library's own code (no CUB, no cooperative-groups
-// grid sync), so every wait carries an explicit time limit.
+// rcm_internal.cuh -- device-side building blocks shared by the library's kernels: the control
+// block, timer and memory-order helpers, and block-level scan/reduce helpers. Everything here is
+// this library's own code (no CUB, no cooperative-groups grid sync), so every wait can carry an
+// explicit time limit.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -11,7 +11,7 @@
 
 namespace rcm {
 
-constexpr int kMaxGridBlocks = 2048;
+constexpr int kMaxGridBlocks = 1024;
 constexpr int kIntMax = 0x7fffffff;
 constexpr unsigned long long kKeyMax = ~0ull;
 
@@ -23,19 +23,22 @@ enum : int {
     kErrTooLarge = 8,   // a size beyond a fixed capacity
 };
 
-// Control block of one ordering: counters, reduction slots, the grid barrier, and the traversal
-// state that CTA 0 publishes after running narrow levels alone.
+// One CTA's slot of the grid exchange: flag = (epoch << 32) | count, written last with release.
+struct alignas(32) ExSlot {
+    unsigned long long flag;
+    unsigned long long key;
+    unsigned long long pad[2];
+};
+
+// Control block of one ordering: counters, the exchange slots, and the traversal state that
+// CTA 0 publishes after running narrow levels alone.
 struct alignas(128) Ctl {
     int status;
     int maxdeg;
     int nbig;              // rows longer than the per-thread sorter handles
     int work_next;         // next work item of a dynamic queue (batched engine)
-    unsigned int bar_arrive;
-    unsigned int bar_gen;
-    int pad1[2];
-    unsigned long long argmin[3];  // ring of min-(degree,id) reduction slots
-    int cnt[3];                    // ring of next-level counters (levels-only sweeps)
-    int pad2;
+    int qtail[3];          // ring of queue / staging tails, indexed by level
+    unsigned int arrive;   // monotone arrival counter of the grid exchange
     // state published by CTA 0 at the end of a run of narrow levels
     int pub_F;       // current frontier size (0 = traversal finished)
     int pub_cur;     // which queue holds the frontier (levels-only sweeps)
@@ -43,8 +46,10 @@ struct alignas(128) Ctl {
     int pub_start;   // label of the frontier's first vertex (labelled sweeps)
     int pub_lastF;   // size of the last non-empty level when finished
     int pub_pad[3];
+    unsigned long long pub_key;    // min (degree, id) key of the last level when finished
     long long stats[8];            // rcm_stats fields, in order
-    int blocksum[kMaxGridBlocks];  // per-CTA totals for grid-wide ordered scans
+    long long phase_ns[8];         // per-phase time of CTA 0 (profile_phases)
+    ExSlot slots[2][kMaxGridBlocks];  // exchange slots, double-buffered by epoch parity
 };
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -64,47 +69,16 @@ __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volati
 // Coherent (L2) load for data written by other CTAs during this kernel.
 __device__ __forceinline__ int ldcg(const int* p) { return __ldcg(p); }
 
-__device__ __forceinline__ unsigned long long pack_key(int deg, int v) {
-    return ((unsigned long long)(unsigned)deg << 32) | (unsigned)v;
+// Bits of a 64-bit claim key left for the in-level order once the level number (at most n + 1)
+// has its own high bits.
+__host__ __device__ inline int claim_order_bits(long long n) {
+    int dbits = 1;
+    while ((1LL << dbits) < n + 2) ++dbits;
+    return 64 - dbits;
 }
 
-// Bounded grid barrier for a cooperative launch of nblocks CTAs. gen is the CTA's view of the
-// barrier generation (kept in a register by thread 0). Returns false if the barrier failed (a
-// wait ran out or another CTA already reported an error); callers then leave the kernel.
-__device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned nblocks, unsigned& gen,
-                                             long long limit_ns) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        unsigned g = gen;
-        __threadfence();
-        unsigned arrived = atomicAdd(&ctl->bar_arrive, 1u);
-        if (arrived == nblocks - 1) {
-            ctl->bar_arrive = 0;
-            __threadfence();
-            atomicExch(&ctl->bar_gen, g + 1);
-        } else {
-            unsigned long long t0 = globaltimer_ns();
-            unsigned spins = 0;
-            while (ld_acquire(&ctl->bar_gen) == g) {
-                if ((++spins & 63u) == 0) {
-                    if (ld_volatile(&ctl->status) & (kErrTimeout | kErrInternal)) { ok = 0; break; }
-                    if ((long long)(globaltimer_ns() - t0) > limit_ns) {
-                        atomicOr(&ctl->status, kErrTimeout);
-                        ok = 0;
-                        break;
-                    }
-                }
-            }
-        }
-        __threadfence();
-        gen = g + 1;
-        if (ok && (ld_volatile(&ctl->status) & (kErrTimeout | kErrInternal))) ok = 0;
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
+__device__ __forceinline__ unsigned long long pack_key(int deg, int v) {
+    return ((unsigned long long)(unsigned)deg << 32) | (unsigned)v;
 }
 
 // ---- block-level helpers (blockDim.x a multiple of 32, at most 1024) ----

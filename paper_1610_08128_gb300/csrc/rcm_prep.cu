@@ -2,18 +2,19 @@
 //
 //  * k_degree_validate: D[v] = number of off-diagonal entries of row v (the degree vector D that
 //    Alg. 3 and Alg. 4 take as input) plus the structural checks of the pattern.
-//  * k_sort_rows_small / k_sort_rows_big: a copy of every row with the diagonal dropped and the
-//    neighbours in increasing (degree, id). Sorting each adjacency row once replaces the per-level
-//    SortPerm of Sec. IV-B: when a frontier vertex scans its sorted row, the children it owns come
-//    out already in (degree, id) order, so the new level is ordered by (parent label, degree, id)
-//    by a prefix sum over parents alone.
+//  * k_sort_rows_small / k_sort_rows_big: every row with the diagonal dropped and the neighbours in
+//    increasing (degree, id), stored as a padded 32-byte row per vertex (7 neighbours + degree) and,
+//    for rows of degree > 7, as a full sorted copy. Sorting each adjacency row once replaces the
+//    per-level SortPerm of Sec. IV-B: when a frontier vertex scans its sorted row, the children it
+//    owns come out already in (degree, id) order, so the new level is ordered by (parent label,
+//    degree, id) by a prefix sum over parents alone.
 //  * k_bw_scatter / k_bw_rows: bandwidth and profile of P A P^T (Sec. II-A).
 #include "rcm_prep.cuh"
 
 namespace rcm {
 
 __global__ void k_degree_validate(int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
-                                  int* __restrict__ deg, int* __restrict__ claim, int* __restrict__ vis,
+                                  int* __restrict__ deg, unsigned long long* __restrict__ claim, int* __restrict__ vis,
                                   int* __restrict__ bigrows, Ctl* ctl, int small_max) {
     __shared__ int s_max;
     if (threadIdx.x == 0) s_max = 0;
@@ -38,7 +39,7 @@ __global__ void k_degree_validate(int n, const int* __restrict__ rowptr, const i
             if (b - a > small_max) bigrows[atomicAdd(&ctl->nbig, 1)] = v;
         }
         deg[v] = d;
-        claim[v] = kIntMax;
+        claim[v] = ~0ull;
         vis[v] = 0;
         local_max = max(local_max, d);
     }
@@ -47,9 +48,18 @@ __global__ void k_degree_validate(int n, const int* __restrict__ rowptr, const i
     if (threadIdx.x == 0) atomicMax(&ctl->maxdeg, s_max);
 }
 
-// Rows of at most kSmallRowMax stored entries: one thread sorts its row in registers/local memory.
+// Padded row of vertex v: its first 7 neighbours in (degree, id) order (-1 where absent) and its
+// degree in slot 7, as two 16-byte stores (one 32-byte sector per vertex).
+__device__ __forceinline__ void store_ell(int4* ell, int v, const int (&r)[8]) {
+    ell[2 * (size_t)v] = make_int4(r[0], r[1], r[2], r[3]);
+    ell[2 * (size_t)v + 1] = make_int4(r[4], r[5], r[6], r[7]);
+}
+
+// Rows of at most kSmallRowMax stored entries: one thread sorts its row, writes the padded row and,
+// when the degree exceeds 7, the whole sorted row into adj (same offsets as the input rows).
 __global__ void k_sort_rows_small(int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
-                                  const int* __restrict__ deg, int* __restrict__ adj, const Ctl* ctl) {
+                                  const int* __restrict__ deg, int* __restrict__ adj, int4* __restrict__ ell,
+                                  const Ctl* ctl) {
     if (ctl->status & kErrBadCsr) return;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         const int a = rowptr[v], b = rowptr[v + 1];
@@ -67,7 +77,13 @@ __global__ void k_sort_rows_small(int n, const int* __restrict__ rowptr, const i
             }
             key[j] = x;
         }
-        for (int i = 0; i < m; ++i) adj[a + i] = (int)(unsigned)(key[i] & 0xffffffffu);
+        int r[8];
+#pragma unroll
+        for (int i = 0; i < 7; ++i) r[i] = i < m ? (int)(unsigned)(key[i] & 0xffffffffu) : -1;
+        r[7] = m;
+        store_ell(ell, v, r);
+        if (m > 7)
+            for (int i = 0; i < m; ++i) adj[a + i] = (int)(unsigned)(key[i] & 0xffffffffu);
     }
 }
 
@@ -95,7 +111,7 @@ __device__ void bitonic_sort_cta(unsigned long long* s, int P) {
 // of at most kBigRowSmem entries; longer rows are sorted by CTA 0 alone in global scratch
 // (scratch holds next_pow2(maxdeg) keys).
 __global__ void k_sort_rows_big(int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
-                                const int* __restrict__ deg, int* __restrict__ adj,
+                                const int* __restrict__ deg, int* __restrict__ adj, int4* __restrict__ ell,
                                 const int* __restrict__ bigrows, const Ctl* ctl,
                                 unsigned long long* __restrict__ scratch) {
     extern __shared__ unsigned long long s_keys[];
@@ -122,6 +138,12 @@ __global__ void k_sort_rows_big(int n, const int* __restrict__ rowptr, const int
         __syncthreads();
         bitonic_sort_cta(s, P);
         for (int i = threadIdx.x; i < m; i += blockDim.x) adj[a + i] = (int)(unsigned)(s[i] & 0xffffffffu);
+        if (threadIdx.x == 0) {
+            int r[8];
+            for (int i = 0; i < 7; ++i) r[i] = i < m ? (int)(unsigned)(s[i] & 0xffffffffu) : -1;
+            r[7] = m;
+            store_ell(ell, v, r);
+        }
         __syncthreads();
     }
     // Huge rows assigned to other CTAs by the stride are picked up here by CTA 0.
@@ -145,6 +167,12 @@ __global__ void k_sort_rows_big(int n, const int* __restrict__ rowptr, const int
         __syncthreads();
         bitonic_sort_cta(scratch, P);
         for (int i = threadIdx.x; i < m; i += blockDim.x) adj[a + i] = (int)(unsigned)(scratch[i] & 0xffffffffu);
+        if (threadIdx.x == 0) {
+            int r[8];
+            for (int i = 0; i < 7; ++i) r[i] = i < m ? (int)(unsigned)(scratch[i] & 0xffffffffu) : -1;
+            r[7] = m;
+            store_ell(ell, v, r);
+        }
         __syncthreads();
     }
 }

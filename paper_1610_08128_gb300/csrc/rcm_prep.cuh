@@ -9,14 +9,15 @@ constexpr int kSmallRowMax = 32;     // rows with at most this many stored entri
 constexpr int kBigRowSmem = 8192;    // rows sorted in shared memory by one CTA (64 KB of keys)
 
 __global__ void k_degree_validate(int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
-                                  int* __restrict__ deg, int* __restrict__ claim, int* __restrict__ vis,
+                                  int* __restrict__ deg, unsigned long long* __restrict__ claim, int* __restrict__ vis,
                                   int* __restrict__ bigrows, Ctl* ctl, int small_max);
 
 __global__ void k_sort_rows_small(int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
-                                  const int* __restrict__ deg, int* __restrict__ adj, const Ctl* ctl);
+                                  const int* __restrict__ deg, int* __restrict__ adj, int4* __restrict__ ell,
+                                  const Ctl* ctl);
 
 __global__ void k_sort_rows_big(int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
-                                const int* __restrict__ deg, int* __restrict__ adj,
+                                const int* __restrict__ deg, int* __restrict__ adj, int4* __restrict__ ell,
                                 const int* __restrict__ bigrows, const Ctl* ctl,
                                 unsigned long long* __restrict__ scratch);
 

@@ -11,34 +11,30 @@
 
 namespace rcm {
 
-__global__ void __launch_bounds__(1024, 1) k_rcm_single(EngineArgs args, int stall) {
-    __shared__ int s_scan[33];
-    __shared__ unsigned long long s_min[32];
-    __shared__ int s_bcast[4];
-    __shared__ int s_cnt;
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads, 1) k_rcm_single(EngineArgs args, int stall) {
+    __shared__ EngineSmem smem;
     if (ld_volatile(&args.ctl->status) & kErrBadCsr) return;
     if (stall && blockIdx.x == 0) return;  // test hook: the other CTAs' first wait runs out
     Engine<false> e;
-    e.init(args, s_scan, s_min, s_bcast, &s_cnt);
+    e.init(args, &smem);
     if (e.run() && blockIdx.x == 0 && threadIdx.x == 0) {
-        for (int i = 0; i < 8; ++i) args.ctl->stats[i] = e.st[i];
+        for (int i = 0; i < 8; ++i) args.ctl->stats[i] = smem.st[i];
+        for (int i = 0; i < 8; ++i) args.ctl->phase_ns[i] = smem.prof[i];
     }
 }
 
-// Reduction slots start at the maximum key; the stored-entry count the host sized the workspace
-// for must match rowptr[n] (otherwise the sorted-adjacency copy would not fit).
+// The stored-entry count the host sized the workspace for must match rowptr[n] (otherwise the
+// sorted-adjacency copy would not fit).
 __global__ void k_init_ctl(Ctl* ctl, int nnz, const int* rowptr_n) {
-    if (threadIdx.x == 0) {
-        ctl->argmin[0] = ctl->argmin[1] = ctl->argmin[2] = kKeyMax;
-        if (*rowptr_n != nnz) ctl->status |= kErrBadCsr;
-    }
+    if (threadIdx.x == 0 && *rowptr_n != nnz) ctl->status |= kErrBadCsr;
 }
 
 // ------------------------------------------------------------------------------------------
 // host side
 
 struct SingleLayout {
-    size_t ctl, pool4, deg, claim, vis, bigrows, adj, total;
+    size_t ctl, pool4, deg, claim, vis, bigrows, adj, ell, total;
 };
 
 static SingleLayout single_layout(long long n, long long nnz) {
@@ -52,23 +48,47 @@ static SingleLayout single_layout(long long n, long long nnz) {
     L.ctl = take(sizeof(Ctl));
     L.pool4 = take(sizeof(int) * 4 * (size_t)std::max(n, 1LL));  // qa | qb | boff | spare; sort scratch in prep
     L.deg = take(sizeof(int) * (size_t)std::max(n, 1LL));
-    L.claim = take(sizeof(int) * (size_t)std::max(n, 1LL));
+    L.claim = take(sizeof(unsigned long long) * (size_t)std::max(n, 1LL));
     L.vis = take(sizeof(int) * (size_t)std::max(n, 1LL));
     L.bigrows = take(sizeof(int) * (size_t)std::max(n, 1LL));
     L.adj = take(sizeof(int) * (size_t)std::max(nnz, 1LL));
+    L.ell = take(sizeof(int4) * 2 * (size_t)std::max(n, 1LL));
     L.total = o;
     return L;
 }
 
-static int g_single_blocks_per_sm[4] = {-1, -1, -1, -1};
+static int g_single_blocks_per_sm[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
 static std::mutex g_single_mu;
+
+static int threads_index(int threads) {
+    switch (threads) {
+        case 32: return 0;
+        case 64: return 1;
+        case 128: return 2;
+        case 256: return 3;
+        case 512: return 4;
+        case 1024: return 5;
+    }
+    return -1;
+}
+
+static const void* single_kernel(int threads) {
+    switch (threads) {
+        case 32: return (const void*)k_rcm_single<32>;
+        case 64: return (const void*)k_rcm_single<64>;
+        case 128: return (const void*)k_rcm_single<128>;
+        case 256: return (const void*)k_rcm_single<256>;
+        case 1024: return (const void*)k_rcm_single<1024>;
+    }
+    return (const void*)k_rcm_single<512>;
+}
 
 static int single_blocks_per_sm(int threads) {
     std::lock_guard<std::mutex> g(g_single_mu);
-    const int idx = threads == 256 ? 0 : threads == 512 ? 1 : 2;
+    const int idx = threads_index(threads);
     if (g_single_blocks_per_sm[idx] < 0) {
         int b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_rcm_single, threads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, single_kernel(threads), threads, 0);
         g_single_blocks_per_sm[idx] = b;
         cudaFuncSetAttribute(k_sort_rows_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(unsigned long long) * kBigRowSmem));
@@ -82,14 +102,21 @@ rcm_status order_single(int32_t n, int64_t nnz, const int32_t* rowptr, const int
     const DeviceInfo& di = device_info();
     rcm_options o{};
     if (opts) o = *opts;
-    const int threads = o.block_threads ? o.block_threads : 1024;
-    if (threads != 256 && threads != 512 && threads != 1024) return RCM_ERR_INVALID_ARG;
+    const int threads = o.block_threads ? o.block_threads : 512;
+    if (threads_index(threads) < 0) return RCM_ERR_INVALID_ARG;
     const int per_sm = single_blocks_per_sm(threads);
     if (per_sm <= 0) return RCM_ERR_CUDA;
     const int max_blocks = std::min(per_sm * di.sms, kMaxGridBlocks);
     int blocks = o.grid_blocks ? o.grid_blocks : di.sms;
     if (blocks < 1 || blocks > max_blocks) return RCM_ERR_INVALID_ARG;
+    // claim keys: (level + 1) in the high bits, the in-level order b * slot + j in the low obits;
+    // slot = (2^obits - 1) / blocks must exceed any slice size (< n)
+    const int obits = claim_order_bits(n);
+    const unsigned long long slot_cap = ((1ull << obits) - 1ull) / (unsigned long long)std::max(n, 1);
+    if ((unsigned long long)blocks > slot_cap) blocks = (int)std::max(1ull, slot_cap);
+    // narrow runs keep the frontier in a shared-memory cache of kCache ids
     int narrow = o.narrow_threshold == 0 ? 2 * threads : (o.narrow_threshold < 0 ? 0 : o.narrow_threshold);
+    narrow = std::min(narrow, kCache);
     const long long limit = o.spin_limit_ns > 0 ? o.spin_limit_ns : 20000000000LL;
 
     const SingleLayout L = single_layout(n, nnz);
@@ -100,10 +127,11 @@ rcm_status order_single(int32_t n, int64_t nnz, const int32_t* rowptr, const int
     Ctl* ctl = (Ctl*)(base + L.ctl);
     int* pool4 = (int*)(base + L.pool4);
     int* deg = (int*)(base + L.deg);
-    int* claim = (int*)(base + L.claim);
+    unsigned long long* claim = (unsigned long long*)(base + L.claim);
     int* vis = (int*)(base + L.vis);
     int* bigrows = (int*)(base + L.bigrows);
     int* adj = (int*)(base + L.adj);
+    int4* ell = (int4*)(base + L.ell);
 
     cudaError_t e = cudaSuccess;
     if (ev) e = cudaEventRecord(ev[0], s);
@@ -114,9 +142,9 @@ rcm_status order_single(int32_t n, int64_t nnz, const int32_t* rowptr, const int
         const int pgrid = (int)std::min<long long>((n + pb - 1) / pb, (long long)di.sms * 16);
         k_degree_validate<<<std::max(pgrid, 1), pb, 0, s>>>(n, rowptr, colidx, deg, claim, vis, bigrows, ctl,
                                                            kSmallRowMax);
-        k_sort_rows_small<<<std::max(pgrid, 1), pb, 0, s>>>(n, rowptr, colidx, deg, adj, ctl);
+        k_sort_rows_small<<<std::max(pgrid, 1), pb, 0, s>>>(n, rowptr, colidx, deg, adj, ell, ctl);
         k_sort_rows_big<<<di.sms * 2, 1024, sizeof(unsigned long long) * kBigRowSmem, s>>>(
-            n, rowptr, colidx, deg, adj, bigrows, ctl, (unsigned long long*)pool4);
+            n, rowptr, colidx, deg, adj, ell, bigrows, ctl, (unsigned long long*)pool4);
         e = cudaGetLastError();
         if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
     }
@@ -125,6 +153,7 @@ rcm_status order_single(int32_t n, int64_t nnz, const int32_t* rowptr, const int
         args.n = n;
         args.v0 = 0;
         args.rowptr = rowptr;
+        args.ell = ell;
         args.adj = adj;
         args.deg = deg;
         args.claim = claim;
@@ -135,11 +164,13 @@ rcm_status order_single(int32_t n, int64_t nnz, const int32_t* rowptr, const int
         args.perm = perm;
         args.ctl = ctl;
         args.narrow_thr = narrow;
+        args.obits = obits;
+        args.profile = o.profile_phases ? 1 : 0;
         args.fused = o.fused_sweeps >= 0 ? 1 : 0;
         args.limit_ns = limit;
         int stall = o.debug_stall_barrier ? 1 : 0;
         void* kargs[] = {&args, &stall};
-        e = cudaLaunchCooperativeKernel((const void*)k_rcm_single, dim3(blocks), dim3(threads), kargs, 0, s);
+        e = cudaLaunchCooperativeKernel(single_kernel(threads), dim3(blocks), dim3(threads), kargs, 0, s);
         if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
     }
     if (e == cudaSuccess) e = enqueue_latch(ctl, stream_latch(s), stats_dev, s);

@@ -37,17 +37,22 @@ class rcm_options(ctypes.Structure):
         ("spin_limit_ns", ctypes.c_int64),
         ("nnz", ctypes.c_int64),
         ("debug_stall_barrier", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("profile_phases", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
 
 class rcm_stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in (
         "components", "sweeps", "traversals", "levels", "max_ecc", "isolated", "narrow_levels", "grid_levels")] + [
-        ("prep_ms", ctypes.c_double), ("traverse_ms", ctypes.c_double)]
+        ("prep_ms", ctypes.c_double), ("traverse_ms", ctypes.c_double), ("phase_ns", ctypes.c_int64 * 8)]
 
     def as_dict(self):
-        return {f: (float if t is ctypes.c_double else int)(getattr(self, f)) for f, t in self._fields_}
+        out = {}
+        for f, t in self._fields_:
+            v = getattr(self, f)
+            out[f] = list(v) if f == "phase_ns" else (float if t is ctypes.c_double else int)(v)
+        return out
 
 
 _lib = None
