@@ -147,6 +147,25 @@ rcm_status rcm_order_host(int32_t n, const int32_t *rowptr, const int32_t *colid
 rcm_status rcm_order_batch(int32_t G, int64_t n_total, const int64_t *goff, const int32_t *rowptr,
                            const int32_t *colidx, int32_t *perm_out, rcm_stream_t stream);
 
+/*
+ * rcm_order_noalloc -- rcm_order for callers that must not allocate device memory (the paper has
+ * no counterpart). Typical callers: an application whose memory framework has already reserved
+ * the device memory for its own caching allocator, or a solver loop with a memory budget fixed
+ * at start-up, where an allocation could fail or stall the device. Same arguments and result as
+ * rcm_order; the workspace is a fixed device array inside this library (about 8 MiB, kept by
+ * every GPU that loads the library until the process exits).
+ *   Limits   n <= 65,536 vertices and rowptr[n] <= 1,048,576 stored entries; larger patterns
+ *            return RCM_ERR_TOO_LARGE before any work is enqueued.
+ *   Set-up   the first call on a device looks up the array's device address (once per device,
+ *            with that device current); make that first call before any stream capture.
+ *   Sharing  every call uses the same array, which keeps the previous call's contents (the call
+ *            clears what must start at zero). Calls whose work overlaps on the GPU (different
+ *            streams, or host threads) race on it and must be serialised by the caller.
+ *   Sync     synchronises `stream`; the return value includes device-detected errors.
+ */
+rcm_status rcm_order_noalloc(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t *perm_out,
+                             rcm_stream_t stream);
+
 /* Synchronises `stream` and returns (and clears) the error latched by earlier calls on it. */
 rcm_status rcm_stream_status(rcm_stream_t stream);
 

@@ -179,3 +179,141 @@ rcm_status order_single(int32_t n, int64_t nnz, const int32_t* rowptr, const int
 }
 
 }  // namespace rcm
+
+namespace rcm {
+
+// ------------------------------------------------------------------------------------------
+// Ordering without any device allocation.
+//
+// Some callers cannot allocate device memory while they run: an application whose memory
+// framework has already reserved the device memory for its own caching allocator, or a solver
+// loop with a fixed memory budget set at start-up in which an allocation could fail or stall
+// the device. rcm_order_noalloc serves them: the whole workspace of the single-graph path lives
+// in the file-scope device array below, so the call allocates nothing. The array holds the
+// workspace of a pattern of at most kNoAllocMaxN vertices and kNoAllocMaxNnz stored entries
+// (about 8 MiB), and every GPU that loads this library keeps it until the process exits.
+
+constexpr int kNoAllocMaxN = 1 << 16;
+constexpr long long kNoAllocMaxNnz = 1LL << 20;
+
+constexpr size_t noalloc_take(size_t bytes) { return (bytes + 255) / 256 * 256; }
+constexpr size_t kNoAllocBytes =
+    noalloc_take(sizeof(Ctl)) + noalloc_take(sizeof(int) * 4 * (size_t)kNoAllocMaxN) +
+    noalloc_take(sizeof(int) * (size_t)kNoAllocMaxN) + noalloc_take(sizeof(unsigned long long) * (size_t)kNoAllocMaxN) +
+    noalloc_take(sizeof(int) * (size_t)kNoAllocMaxN) + noalloc_take(sizeof(int) * (size_t)kNoAllocMaxN) +
+    noalloc_take(sizeof(int) * (size_t)kNoAllocMaxNnz) + noalloc_take(sizeof(int4) * 2 * (size_t)kNoAllocMaxN);
+
+static __device__ __align__(256) unsigned char g_noalloc_ws[kNoAllocBytes];
+
+// Device address of g_noalloc_ws on the current device. In host code the symbol itself is only a
+// host-side stand-in, so the address is looked up once per device (with that device current)
+// and cached.
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[64];
+
+static rcm_status noalloc_workspace(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (dev < 0 || dev >= 64) return RCM_ERR_CUDA;
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_ws);
+        if (e != cudaSuccess || !p) return e != cudaSuccess ? cuda_status(e) : RCM_ERR_CUDA;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return RCM_OK;
+}
+
+rcm_status order_single_noalloc(int32_t n, const int32_t* rowptr, const int32_t* colidx, int32_t* perm,
+                                cudaStream_t s) {
+    if (n < 0) return RCM_ERR_INVALID_ARG;
+    if (n == 0) return RCM_OK;
+    if (!rowptr || !perm) return RCM_ERR_INVALID_ARG;
+    if (n > kNoAllocMaxN) return RCM_ERR_TOO_LARGE;
+    void* ws = nullptr;
+    rcm_status st = noalloc_workspace(&ws);
+    if (st != RCM_OK) return st;
+    // stored-entry count: one 4-byte read into host stack memory
+    int nnz = 0;
+    cudaError_t e = cudaMemcpyAsync(&nnz, rowptr + n, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (nnz < 0) return RCM_ERR_BAD_CSR;
+    if (nnz > kNoAllocMaxNnz) return RCM_ERR_TOO_LARGE;
+    if (nnz > 0 && !colidx) return RCM_ERR_INVALID_ARG;
+    const SingleLayout L = single_layout(n, nnz);
+    if (L.total > kNoAllocBytes) return RCM_ERR_TOO_LARGE;
+
+    const DeviceInfo& di = device_info();
+    const int threads = 512;
+    const int per_sm = single_blocks_per_sm(threads);
+    if (per_sm <= 0) return RCM_ERR_CUDA;
+    int blocks = std::min(di.sms, std::min(per_sm * di.sms, kMaxGridBlocks));
+    const int obits = claim_order_bits(n);
+    const unsigned long long slot_cap = ((1ull << obits) - 1ull) / (unsigned long long)std::max(n, 1);
+    if ((unsigned long long)blocks > slot_cap) blocks = (int)std::max(1ull, slot_cap);
+
+    char* base = (char*)ws;
+    Ctl* ctl = (Ctl*)(base + L.ctl);
+    int* pool4 = (int*)(base + L.pool4);
+    int* deg = (int*)(base + L.deg);
+    unsigned long long* claim = (unsigned long long*)(base + L.claim);
+    int* vis = (int*)(base + L.vis);
+    int* bigrows = (int*)(base + L.bigrows);
+    int* adj = (int*)(base + L.adj);
+    int4* ell = (int4*)(base + L.ell);
+    // the array keeps the previous call's contents: the control block must start at zero; every
+    // other per-vertex array is initialised by the kernels below
+    e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), s);
+    if (e == cudaSuccess) {
+        k_init_ctl<<<1, 32, 0, s>>>(ctl, nnz, rowptr + n);
+        const int pb = 256;
+        const int pgrid = (int)std::min<long long>((n + pb - 1) / pb, (long long)di.sms * 16);
+        k_degree_validate<<<std::max(pgrid, 1), pb, 0, s>>>(n, rowptr, colidx, deg, claim, vis, bigrows, ctl,
+                                                           kSmallRowMax);
+        k_sort_rows_small<<<std::max(pgrid, 1), pb, 0, s>>>(n, rowptr, colidx, deg, adj, ell, ctl);
+        k_sort_rows_big<<<di.sms * 2, 1024, sizeof(unsigned long long) * kBigRowSmem, s>>>(
+            n, rowptr, colidx, deg, adj, ell, bigrows, ctl, (unsigned long long*)pool4);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        EngineArgs args;
+        args.n = n;
+        args.v0 = 0;
+        args.rowptr = rowptr;
+        args.ell = ell;
+        args.adj = adj;
+        args.deg = deg;
+        args.claim = claim;
+        args.vis = vis;
+        args.qa = pool4;
+        args.qb = pool4 + n;
+        args.boff = pool4 + 2 * (size_t)n;
+        args.perm = perm;
+        args.ctl = ctl;
+        args.narrow_thr = std::min(2 * threads, kCache);
+        args.obits = obits;
+        args.profile = 0;
+        args.fused = 1;
+        args.limit_ns = 20000000000LL;
+        int stall = 0;
+        void* kargs[] = {&args, &stall};
+        e = cudaLaunchCooperativeKernel(single_kernel(threads), dim3(blocks), dim3(threads), kargs, 0, s);
+    }
+    // synchronous: the device-detected status is read back from the control block
+    int bits = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, &ctl->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    return status_from_bits(bits);
+}
+
+}  // namespace rcm
+
+extern "C" rcm_status rcm_order_noalloc(int32_t n, const int32_t* rowptr, const int32_t* colidx, int32_t* perm_out,
+                                        rcm_stream_t stream) {
+    return rcm::order_single_noalloc(n, rowptr, colidx, perm_out, (cudaStream_t)stream);
+}

@@ -76,6 +76,7 @@ def load():
         "rcm_order": ([I32, P, P, P, P], ctypes.c_int),
         "rcm_order_ex": ([I32, P, P, P, ctypes.POINTER(rcm_options), ctypes.POINTER(rcm_stats), P], ctypes.c_int),
         "rcm_order_host": ([I32, P, P, P, P], ctypes.c_int),
+        "rcm_order_noalloc": ([I32, P, P, P, P], ctypes.c_int),
         "rcm_order_batch": ([I32, I64, P, P, P, P, P], ctypes.c_int),
         "rcm_stream_status": ([P], ctypes.c_int),
         "rcm_workspace_bytes": ([I32, I64], SZ),
@@ -146,6 +147,11 @@ def rcm_order_ex(n, rowptr, colidx, perm_out, options: rcm_options | None = None
 def rcm_order_host(n, rowptr, colidx, perm_out, stream=None) -> int:
     return load().rcm_order_host(int(n), _ptr(rowptr, False, _i32()), _ptr(colidx, False, _i32()),
                                  _ptr(perm_out, False, _i32()), _stream(stream))
+
+
+def rcm_order_noalloc(n, rowptr, colidx, perm_out, stream=None) -> int:
+    return load().rcm_order_noalloc(int(n), _ptr(rowptr, True, _i32()), _ptr(colidx, True, _i32()),
+                                    _ptr(perm_out, True, _i32()), _stream(stream))
 
 
 def rcm_order_batch(G, n_total, goff, rowptr, colidx, perm_out, stream=None) -> int:
