@@ -166,6 +166,59 @@ rcm_status rcm_order_batch(int32_t G, int64_t n_total, const int64_t *goff, cons
 rcm_status rcm_order_noalloc(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t *perm_out,
                              rcm_stream_t stream);
 
+/*
+ * Serving (continuous batching; no counterpart in the paper, which orders one matrix at a time).
+ * A server owns a device arena of hbm_budget_bytes (allocated once at creation) and up to
+ * max_inflight concurrent requests. Each request needs one arena region: its CSR when given in
+ * host memory, its output when the caller's buffer is in host memory, and the ordering's
+ * workspace (about 68 bytes per vertex plus 4 bytes per stored entry). Requests are admitted in
+ * arrival order as regions and slots free up; each admitted request runs on its own stream as a
+ * single-CTA kernel, so requests that arrive while others are on the GPU run alongside them.
+ * Results are bit-identical to rcm_order on the same pattern.
+ */
+typedef struct rcm_server rcm_server;
+
+typedef struct {
+    int64_t submitted, completed, failed, cancelled;
+    int64_t waiting;            /* submitted, not admitted yet                                      */
+    int64_t running;            /* admitted, not finished                                           */
+    int64_t max_running;        /* largest number of requests on the GPU at once                    */
+    int64_t arena_bytes;        /* budget                                                           */
+    int64_t arena_peak_bytes;   /* largest arena use                                                */
+    double latency_p50_s;       /* completion minus submission time, over completed requests       */
+    double latency_p99_s;
+    double latency_max_s;
+} rcm_server_stats;
+
+/* Creates a server on the current device. max_inflight in [1, 4096]. */
+rcm_status rcm_server_create(size_t hbm_budget_bytes, int32_t max_inflight, rcm_server **out);
+
+/*
+ * Submits one ordering request and returns its ticket. rowptr/colidx may be host or device
+ * memory, perm_out host or device memory (pinned host memory gives the fastest copies); all must
+ * stay valid and unmodified until rcm_poll/rcm_wait reports the request finished. A request
+ * that can never fit the budget returns RCM_ERR_TOO_LARGE (no ticket).
+ */
+rcm_status rcm_submit(rcm_server *srv, int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *colidx,
+                      int32_t *perm_out, uint64_t *ticket);
+
+/* RCM_ERR_NOT_READY while the request runs or waits; otherwise its final status, after which
+   the ticket is forgotten (a later poll returns RCM_ERR_UNKNOWN_TICKET). */
+rcm_status rcm_poll(rcm_server *srv, uint64_t ticket);
+
+/* Blocks until the request finishes; returns its final status and forgets the ticket. */
+rcm_status rcm_wait(rcm_server *srv, uint64_t ticket);
+
+/* Withdraws a request that has not been admitted yet (RCM_OK); a running request cannot be
+   withdrawn (RCM_ERR_NOT_READY). */
+rcm_status rcm_cancel(rcm_server *srv, uint64_t ticket);
+
+/* Counters and latency percentiles of the requests seen so far. */
+rcm_status rcm_server_info(rcm_server *srv, rcm_server_stats *out);
+
+/* Drops requests not admitted yet, waits for running ones, and frees the server. */
+rcm_status rcm_server_destroy(rcm_server *srv);
+
 /* Synchronises `stream` and returns (and clears) the error latched by earlier calls on it. */
 rcm_status rcm_stream_status(rcm_stream_t stream);
 

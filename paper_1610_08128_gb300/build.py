@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ_DIR = os.path.join(HERE, "_build")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "librcm_gb300.so")
-SOURCES = ["rcm_capi.cu", "rcm_prep.cu", "rcm_single.cu", "rcm_batch.cu"]
+SOURCES = ["rcm_capi.cu", "rcm_prep.cu", "rcm_single.cu", "rcm_batch.cu", "rcm_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xcompiler", "-Wall"]
 

@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(kThreads) k_rcm_batch(BatchArgs b) {
         a.boff = b.boff + v0;
         a.perm = b.perm + v0;
         a.ctl = b.ctl;
+        a.status = &b.ctl->status;
         a.narrow_thr = 0x7fffffff;
         a.obits = claim_order_bits(n);
         a.profile = 0;

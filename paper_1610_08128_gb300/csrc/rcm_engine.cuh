@@ -64,7 +64,8 @@ struct EngineArgs {
     int* qb;                     // this graph's queue / staging buffer (n ints)
     int* boff;                   // this graph's per-frontier offsets (n ints)
     int* perm;                   // this graph's output segment (n ints); global ids while running
-    Ctl* ctl;
+    Ctl* ctl;                    // grid control block (whole-grid executor only)
+    int* status;                 // where device-detected error bits are ORed
     int narrow_thr;
     int fused;
     int obits;                   // low bits of a key holding the in-level order
@@ -80,9 +81,9 @@ struct EngineSmem {
     long long st[8];             // statistics (rcm_stats order), updated by thread 0
     long long prof[8];           // per-phase ns (profile), updated by thread 0 of CTA 0
     unsigned long long prof_t;   // timestamp of the last phase boundary
-    int scan[33];
-    int acc_cnt;                 // CTA accumulators feeding the exchange
-    unsigned long long acc_key;
+    int scan[64];
+    int acc_cnt;                 // CTA count accumulator feeding the exchange
+    unsigned long long wkey[32]; // per-warp min keys of the last accumulate()
     int ex[4];                   // exchange results: total, pre, maxcnt
     unsigned long long ex_key;
     int bc[8];
@@ -109,6 +110,7 @@ struct Engine {
     const EngineArgs* a;   // in shared memory (keeps the per-thread register footprint small)
     unsigned epoch;
     int sweep_id;
+    int scan_par;          // alternates between consecutive CTA scans (see block_excl_scan)
     EngineSmem* sm;
 
     // All threads call; args are copied to shared memory by thread 0.
@@ -120,12 +122,13 @@ struct Engine {
             for (int i = 0; i < 8; ++i) smem->prof[i] = 0;
             smem->prof_t = globaltimer_ns();
             smem->acc_cnt = 0;
-            smem->acc_key = kKeyMax;
+            for (int i = 0; i < 32; ++i) smem->wkey[i] = kKeyMax;
         }
         __syncthreads();
         a = &smem->args;
         epoch = 0;
         sweep_id = 0;
+        scan_par = 0;
     }
 
     // Phase boundary: the time since the previous boundary is charged to phase `ph`.
@@ -137,6 +140,12 @@ struct Engine {
         }
     }
 
+    __device__ int cta_scan(int x, int* total) {
+        const int r = block_excl_scan(x, total, sm->scan, scan_par);
+        scan_par ^= 1;
+        return r;
+    }
+
     __device__ void stat_add(int i, long long v) {
         if (threadIdx.x == 0) sm->st[i] += v;
     }
@@ -144,9 +153,14 @@ struct Engine {
         if (threadIdx.x == 0 && v > sm->st[i]) sm->st[i] = v;
     }
     __device__ bool in_graph(int v) const { return (unsigned)(v - a->v0) < (unsigned)a->n; }
-    __device__ void fail(int bits) { atomicOr(&a->ctl->status, bits); }
+    __device__ void fail(int bits) { atomicOr(a->status, bits); }
     __device__ int cta_rank() const { return kCtaOnly ? 0 : (int)blockIdx.x; }
     __device__ int cta_count() const { return kCtaOnly ? 1 : (int)gridDim.x; }
+
+    // Bring a vertex's padded row into L2 ahead of the level that will read it.
+    __device__ void prefetch_row(int u) const {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a->ell + 2 * (size_t)u));
+    }
 
     __device__ void load_row(int u, int (&r)[8]) const {
         const int4* p = a->ell + 2 * (size_t)u;
@@ -155,7 +169,9 @@ struct Engine {
         r[4] = y.x; r[5] = y.y; r[6] = y.z; r[7] = y.w;
     }
 
-    // Per-thread (count, key) partials into the CTA accumulators (warp-reduced first).
+    // Per-thread (count, key) partials: counts go to a shared counter, keys to one slot per warp
+    // (a 64-bit shared-memory min would need a compare-and-swap loop). Consumers read the CTA
+    // min with cta_key() after a barrier.
     __device__ void accumulate(int cnt, unsigned long long key) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -165,8 +181,16 @@ struct Engine {
         }
         if ((threadIdx.x & 31) == 0) {
             if (cnt) atomicAdd(&sm->acc_cnt, cnt);
-            if (key != kKeyMax) atomicMin(&sm->acc_key, key);
+            sm->wkey[threadIdx.x >> 5] = key;
         }
+    }
+
+    // Min over the per-warp keys of the last accumulate(); call after a barrier.
+    __device__ unsigned long long cta_key() const {
+        unsigned long long k = kKeyMax;
+        const int nw = blockDim.x >> 5;
+        for (int w = 0; w < nw; ++w) k = sm->wkey[w] < k ? sm->wkey[w] : k;
+        return k;
     }
 
     // ---- the exchange: grid barrier carrying the accumulated (count, key) of every CTA ----
@@ -178,12 +202,9 @@ struct Engine {
             r.total = sm->acc_cnt;
             r.pre = 0;
             r.maxcnt = r.total;
-            r.key = sm->acc_key;
+            r.key = cta_key();
             __syncthreads();
-            if (threadIdx.x == 0) {
-                sm->acc_cnt = 0;
-                sm->acc_key = kKeyMax;
-            }
+            if (threadIdx.x == 0) sm->acc_cnt = 0;
             return true;
         }
         const unsigned e = ++epoch;
@@ -194,9 +215,8 @@ struct Engine {
             if (threadIdx.x == 0) {
                 ExSlot* sl = &c->slots[e & 1][b];
                 sl->flag = ((unsigned long long)e << 32) | (unsigned)sm->acc_cnt;
-                sl->key = sm->acc_key;
+                sl->key = cta_key();
                 sm->acc_cnt = 0;
-                sm->acc_key = kKeyMax;
                 red_release_add(&c->arrive, 1u);
                 const unsigned target = e * (unsigned)B;
                 if ((int)(ld_acquire(&c->arrive) - target) < 0) {
@@ -317,7 +337,7 @@ struct Engine {
             }
             const int c = __popc(mask);
             int tot;
-            const int ex = block_excl_scan(c, &tot, sm->scan);
+            const int ex = cta_scan(c, &tot);
             if (tot) {
                 if (threadIdx.x == 0) sm->bc[0] = atomicAdd(tail, tot);
                 __syncthreads();
@@ -326,6 +346,7 @@ struct Engine {
 #pragma unroll
                 for (int k = 0; k < kEllNb; ++k)
                     if (mask & (1u << k)) {
+                        prefetch_row(r[k]);
                         nxt[pos] = r[k];
                         if (ncache && pos < kCache) ncache[pos] = r[k];
                         ++pos;
@@ -375,12 +396,9 @@ struct Engine {
                         __syncthreads();
                         tick(kPhExpand);
                         const int cnt = sm->acc_cnt;
-                        const unsigned long long key = sm->acc_key;
+                        const unsigned long long key = cta_key();
                         __syncthreads();
-                        if (threadIdx.x == 0) {
-                            sm->acc_cnt = 0;
-                            sm->acc_key = kKeyMax;
-                        }
+                        if (threadIdx.x == 0) sm->acc_cnt = 0;
                         stat_add(kStNarrow, 1);
                         if (cnt == 0) {
                             lk = key;
@@ -565,7 +583,7 @@ struct Engine {
                 }
             }
             int tot;
-            const int ex = block_excl_scan(c, &tot, sm->scan);
+            const int ex = cta_scan(c, &tot);
             if (j0 == 0) {
                 m0 = mask;
                 off0 = ex;
@@ -607,6 +625,7 @@ struct Engine {
 #pragma unroll
             for (int k = 0; k < kEllNb; ++k)
                 if (mask & (1u << k)) {
+                    prefetch_row(rw[k]);
                     dst[pos] = rw[k];
                     if (lab_base >= 0) {
                         const int lab = lab_base + pos;
@@ -681,9 +700,7 @@ struct Engine {
                         phase_a(d, 0, cur, u0, r0);
                         __syncthreads();
                         tick(kPhClaim);
-                        const unsigned long long key = sm->acc_key;
-                        __syncthreads();
-                        if (threadIdx.x == 0) sm->acc_key = kKeyMax;
+                        const unsigned long long key = cta_key();
                         if (threadIdx.x == 0) sm->tail = 0;
                         __syncthreads();
                         Slice nxt;
@@ -827,7 +844,7 @@ struct Engine {
             const int i = i0 + (int)threadIdx.x;
             const int f = (i < hi && __ldg(a->deg + a->v0 + i) == 0) ? 1 : 0;
             int tot;
-            const int ex = block_excl_scan(f, &tot, sm->scan);
+            const int ex = cta_scan(f, &tot);
             if (f) {
                 const int lab = carry + ex;
                 a->perm[n - 1 - lab] = a->v0 + i;

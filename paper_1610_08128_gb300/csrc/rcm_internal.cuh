@@ -93,29 +93,22 @@ __device__ __forceinline__ int warp_incl_scan(int x) {
     return x;
 }
 
-// Exclusive scan of x over the CTA in thread order; *total receives the sum. Uses 33 ints of smem.
-__device__ __forceinline__ int block_excl_scan(int x, int* total, int* smem) {
+// Exclusive scan of x over the CTA in thread order; *total receives the sum. smem: 64 ints used
+// as two halves; callers alternate `parity` (0, 1, 0, ...) between consecutive calls, so one
+// barrier suffices: a call writes the half that the previous call did not use, and every thread
+// has finished reading a half before the barrier of the next call lets anyone overwrite it.
+__device__ __forceinline__ int block_excl_scan(int x, int* total, int* smem, int parity) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int incl = warp_incl_scan(x);
-    if (lane == 31) smem[wid] = incl;
+    int* half = smem + parity * 32;
+    const int incl = warp_incl_scan(x);
+    if (lane == 31) half[wid] = incl;
     __syncthreads();
-    if (wid == 0) {
-        int v = lane < nw ? smem[lane] : 0;
-        int vi = warp_incl_scan(v);
-        if (lane < nw) smem[lane] = vi - v;
-        if (lane == 31) smem[32] = vi;
-    }
-    __syncthreads();
-    int r = smem[wid] + incl - x;
-    *total = smem[32];
-    __syncthreads();
-    return r;
-}
-
-__device__ __forceinline__ int block_sum(int x, int* smem) {
-    int t;
-    block_excl_scan(x, &t, smem);
-    return t;
+    // every warp scans the warp totals itself: lane l holds total l
+    const int t = lane < nw ? half[lane] : 0;
+    const int ti = warp_incl_scan(t);
+    const int before = wid > 0 ? __shfl_sync(0xffffffffu, ti, wid - 1) : 0;
+    *total = __shfl_sync(0xffffffffu, ti, 31);
+    return before + incl - x;
 }
 
 __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long x) {

@@ -48,63 +48,13 @@ __global__ void k_degree_validate(int n, const int* __restrict__ rowptr, const i
     if (threadIdx.x == 0) atomicMax(&ctl->maxdeg, s_max);
 }
 
-// Padded row of vertex v: its first 7 neighbours in (degree, id) order (-1 where absent) and its
-// degree in slot 7, as two 16-byte stores (one 32-byte sector per vertex).
-__device__ __forceinline__ void store_ell(int4* ell, int v, const int (&r)[8]) {
-    ell[2 * (size_t)v] = make_int4(r[0], r[1], r[2], r[3]);
-    ell[2 * (size_t)v + 1] = make_int4(r[4], r[5], r[6], r[7]);
-}
-
-// Rows of at most kSmallRowMax stored entries: one thread sorts its row, writes the padded row and,
-// when the degree exceeds 7, the whole sorted row into adj (same offsets as the input rows).
+// Rows of at most kSmallRowMax stored entries: one thread per row (sort_small_row).
 __global__ void k_sort_rows_small(int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
                                   const int* __restrict__ deg, int* __restrict__ adj, int4* __restrict__ ell,
                                   const Ctl* ctl) {
     if (ctl->status & kErrBadCsr) return;
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        const int a = rowptr[v], b = rowptr[v + 1];
-        if (b - a > kSmallRowMax) continue;
-        unsigned long long key[kSmallRowMax];
-        int m = 0;
-        for (int k = a; k < b; ++k) {
-            const int w = colidx[k];
-            if (w == v) continue;
-            const unsigned long long x = pack_key(__ldg(deg + w), w);
-            int j = m++;
-            while (j > 0 && key[j - 1] > x) {
-                key[j] = key[j - 1];
-                --j;
-            }
-            key[j] = x;
-        }
-        int r[8];
-#pragma unroll
-        for (int i = 0; i < 7; ++i) r[i] = i < m ? (int)(unsigned)(key[i] & 0xffffffffu) : -1;
-        r[7] = m;
-        store_ell(ell, v, r);
-        if (m > 7)
-            for (int i = 0; i < m; ++i) adj[a + i] = (int)(unsigned)(key[i] & 0xffffffffu);
-    }
-}
-
-// Bitonic sort of P (a power of two) keys held in `s` (shared or global memory) by one CTA.
-__device__ void bitonic_sort_cta(unsigned long long* s, int P) {
-    for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < P; i += blockDim.x) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const bool asc = (i & k) == 0;
-                    unsigned long long x = s[i], y = s[ixj];
-                    if ((x > y) == asc) {
-                        s[i] = y;
-                        s[ixj] = x;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        if (rowptr[v + 1] - rowptr[v] <= kSmallRowMax) sort_small_row(v, rowptr, colidx, deg, adj, ell);
 }
 
 // Rows longer than the per-thread sorter: one CTA per row, bitonic sort in shared memory for rows

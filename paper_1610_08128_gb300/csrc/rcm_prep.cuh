@@ -8,6 +8,108 @@ namespace rcm {
 constexpr int kSmallRowMax = 32;     // rows with at most this many stored entries: per-thread sort
 constexpr int kBigRowSmem = 8192;    // rows sorted in shared memory by one CTA (64 KB of keys)
 
+// Padded row of vertex v: its first 7 neighbours in (degree, id) order (-1 where absent) and its
+// degree in slot 7, as two 16-byte stores (one 32-byte sector per vertex).
+__device__ __forceinline__ void store_ell(int4* ell, int v, const int (&r)[8]) {
+    ell[2 * (size_t)v] = make_int4(r[0], r[1], r[2], r[3]);
+    ell[2 * (size_t)v + 1] = make_int4(r[4], r[5], r[6], r[7]);
+}
+
+// Bitonic sort of P (a power of two) keys held in `s` (shared or global memory) by one CTA.
+__device__ __forceinline__ void bitonic_sort_cta(unsigned long long* s, int P) {
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const bool asc = (i & k) == 0;
+                    unsigned long long x = s[i], y = s[ixj];
+                    if ((x > y) == asc) {
+                        s[i] = y;
+                        s[ixj] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Degree of row v (off-diagonal entries) with the structural checks of the row; returns false if
+// the row is malformed (bad bounds or a column outside [0, n)).
+__device__ __forceinline__ bool row_degree(int n, int nnz, const int* __restrict__ rowptr,
+                                           const int* __restrict__ colidx, int v, int& d) {
+    const int a = rowptr[v], b = rowptr[v + 1];
+    d = 0;
+    if (a < 0 || b < a || b > nnz) return false;
+    bool ok = true;
+    for (int k = a; k < b; ++k) {
+        const int w = colidx[k];
+        if ((unsigned)w >= (unsigned)n) ok = false;
+        else if (w != v) ++d;
+    }
+    return ok;
+}
+
+// Sorted row of a vertex with at most kSmallRowMax stored entries, by one thread: the padded row
+// and, for degree > 7, the full sorted row in adj (same offsets as the input row).
+__device__ __forceinline__ void sort_small_row(int v, const int* __restrict__ rowptr, const int* __restrict__ colidx,
+                                               const int* __restrict__ deg, int* __restrict__ adj,
+                                               int4* __restrict__ ell) {
+    const int a = rowptr[v], b = rowptr[v + 1];
+    unsigned long long key[kSmallRowMax];
+    int m = 0;
+    for (int k = a; k < b; ++k) {
+        const int w = colidx[k];
+        if (w == v) continue;
+        const unsigned long long x = pack_key(__ldg(deg + w), w);
+        int j = m++;
+        while (j > 0 && key[j - 1] > x) {
+            key[j] = key[j - 1];
+            --j;
+        }
+        key[j] = x;
+    }
+    int r[8];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) r[i] = i < m ? (int)(unsigned)(key[i] & 0xffffffffu) : -1;
+    r[7] = m;
+    store_ell(ell, v, r);
+    if (m > 7)
+        for (int i = 0; i < m; ++i) adj[a + i] = (int)(unsigned)(key[i] & 0xffffffffu);
+}
+
+// Sorted row of one long row by the whole CTA: keys gathered into `s` (kBigRowSmem keys of shared
+// memory, or global scratch of next_pow2(degree) keys), bitonic-sorted, written to adj and ell.
+// s_m: one shared int.
+__device__ __forceinline__ void sort_big_row_cta(int v, const int* __restrict__ rowptr,
+                                                 const int* __restrict__ colidx, const int* __restrict__ deg,
+                                                 int* __restrict__ adj, int4* __restrict__ ell,
+                                                 unsigned long long* s, int* s_m) {
+    const int a = rowptr[v], b = rowptr[v + 1];
+    const int m = deg[v];
+    int P = 1;
+    while (P < m) P <<= 1;
+    if (threadIdx.x == 0) *s_m = 0;
+    __syncthreads();
+    for (int k = a + threadIdx.x; k < b; k += blockDim.x) {
+        const int w = colidx[k];
+        if (w != v) s[atomicAdd(s_m, 1)] = pack_key(__ldg(deg + w), w);
+    }
+    __syncthreads();
+    for (int i = m + threadIdx.x; i < P; i += blockDim.x) s[i] = kKeyMax;
+    __syncthreads();
+    bitonic_sort_cta(s, P);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) adj[a + i] = (int)(unsigned)(s[i] & 0xffffffffu);
+    if (threadIdx.x == 0) {
+        int r[8];
+        for (int i = 0; i < 7; ++i) r[i] = i < m ? (int)(unsigned)(s[i] & 0xffffffffu) : -1;
+        r[7] = m;
+        store_ell(ell, v, r);
+    }
+    __syncthreads();
+}
+
 __global__ void k_degree_validate(int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
                                   int* __restrict__ deg, unsigned long long* __restrict__ claim, int* __restrict__ vis,
                                   int* __restrict__ bigrows, Ctl* ctl, int small_max);

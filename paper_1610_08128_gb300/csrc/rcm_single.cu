@@ -163,6 +163,7 @@ rcm_status order_single(int32_t n, int64_t nnz, const int32_t* rowptr, const int
         args.boff = pool4 + 2 * (size_t)n;
         args.perm = perm;
         args.ctl = ctl;
+        args.status = &ctl->status;
         args.narrow_thr = narrow;
         args.obits = obits;
         args.profile = o.profile_phases ? 1 : 0;
@@ -294,6 +295,7 @@ rcm_status order_single_noalloc(int32_t n, const int32_t* rowptr, const int32_t*
         args.boff = pool4 + 2 * (size_t)n;
         args.perm = perm;
         args.ctl = ctl;
+        args.status = &ctl->status;
         args.narrow_thr = std::min(2 * threads, kCache);
         args.obits = obits;
         args.profile = 0;

@@ -55,6 +55,15 @@ class rcm_stats(ctypes.Structure):
         return out
 
 
+class rcm_server_stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in (
+        "submitted", "completed", "failed", "cancelled", "waiting", "running", "max_running", "arena_bytes",
+        "arena_peak_bytes")] + [(f, ctypes.c_double) for f in ("latency_p50_s", "latency_p99_s", "latency_max_s")]
+
+    def as_dict(self):
+        return {f: (float if t is ctypes.c_double else int)(getattr(self, f)) for f, t in self._fields_}
+
+
 _lib = None
 
 
@@ -81,6 +90,13 @@ def load():
         "rcm_stream_status": ([P], ctypes.c_int),
         "rcm_workspace_bytes": ([I32, I64], SZ),
         "rcm_bandwidth_profile": ([I32, P, P, P, ctypes.POINTER(I64), ctypes.POINTER(I64), P], ctypes.c_int),
+        "rcm_server_create": ([SZ, I32, ctypes.POINTER(P)], ctypes.c_int),
+        "rcm_submit": ([P, I32, I64, P, P, P, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+        "rcm_poll": ([P, ctypes.c_uint64], ctypes.c_int),
+        "rcm_wait": ([P, ctypes.c_uint64], ctypes.c_int),
+        "rcm_cancel": ([P, ctypes.c_uint64], ctypes.c_int),
+        "rcm_server_info": ([P, ctypes.POINTER(rcm_server_stats)], ctypes.c_int),
+        "rcm_server_destroy": ([P], ctypes.c_int),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -176,6 +192,43 @@ def rcm_bandwidth_profile(n, rowptr, colidx, perm, stream=None):
                                       _ptr(perm, True, _i32()), ctypes.byref(bw), ctypes.byref(prof),
                                       _stream(stream))
     return st, int(bw.value), int(prof.value)
+
+
+def rcm_server_create(hbm_budget_bytes, max_inflight):
+    """Returns (status, server handle)."""
+    h = ctypes.c_void_p()
+    st = load().rcm_server_create(int(hbm_budget_bytes), int(max_inflight), ctypes.byref(h))
+    return st, h
+
+
+def rcm_submit(srv, n, nnz, rowptr, colidx, perm_out):
+    """Returns (status, ticket). Buffers: torch tensors (host or CUDA) or raw pointers."""
+    t = ctypes.c_uint64(0)
+    st = load().rcm_submit(srv, int(n), int(nnz), _ptr(rowptr, None, _i32()), _ptr(colidx, None, _i32()),
+                           _ptr(perm_out, None, _i32()), ctypes.byref(t))
+    return st, int(t.value)
+
+
+def rcm_poll(srv, ticket) -> int:
+    return load().rcm_poll(srv, int(ticket))
+
+
+def rcm_wait(srv, ticket) -> int:
+    return load().rcm_wait(srv, int(ticket))
+
+
+def rcm_cancel(srv, ticket) -> int:
+    return load().rcm_cancel(srv, int(ticket))
+
+
+def rcm_server_info(srv):
+    st = rcm_server_stats()
+    s = load().rcm_server_info(srv, ctypes.byref(st))
+    return s, st.as_dict()
+
+
+def rcm_server_destroy(srv) -> int:
+    return load().rcm_server_destroy(srv)
 
 
 def check(status: int, what: str = "") -> None:
