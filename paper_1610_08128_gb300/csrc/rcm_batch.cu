@@ -85,6 +85,11 @@ __global__ void __launch_bounds__(kThreads) k_rcm_batch(BatchArgs b) {
         a.narrow_thr = 0x7fffffff;
         a.obits = claim_order_bits(n);
         a.profile = 0;
+        a.cc_parent = a.cc_size = a.cc_roots = a.cc_gidx = nullptr;
+        a.cc_key = a.cc_gkey = nullptr;
+        a.cc_tab = nullptr;
+        a.cc_cap = 0;
+        a.cc_big = 0;
         a.fused = 1;
         a.limit_ns = 0;
         __syncthreads();

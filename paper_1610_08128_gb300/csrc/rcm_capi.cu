@@ -6,6 +6,7 @@
 
 #include "rcm_host.hpp"
 #include "rcm_internal.cuh"
+#include "rcm_cc.cuh"
 #include "rcm_prep.cuh"
 
 namespace rcm {

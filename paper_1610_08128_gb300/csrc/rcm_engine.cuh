@@ -43,6 +43,7 @@
 // largest count and the min key. Every wait is bounded by a %globaltimer limit.
 #pragma once
 
+#include "rcm_cc.cuh"
 #include "rcm_internal.cuh"
 
 namespace rcm {
@@ -71,6 +72,16 @@ struct EngineArgs {
     int obits;                   // low bits of a key holding the in-level order
     int profile;                 // accumulate per-phase time (CTA 0, thread 0)
     long long limit_ns;
+    // concurrent components (whole-grid executor only)
+    int* cc_parent;              // n ints
+    int* cc_size;                // n ints (indexed by root)
+    unsigned long long* cc_key;  // n keys (indexed by root)
+    int* cc_roots;               // cc_cap ints
+    unsigned long long* cc_gkey; // next_pow2(cc_cap) keys (sort scratch beyond shared memory)
+    int* cc_gidx;                // next_pow2(cc_cap) ints
+    int4* cc_tab;                // cc_cap entries: (start vertex, first label, size, root)
+    int cc_cap;                  // most components ordered concurrently (else one by one)
+    int cc_big;                  // components at least this large run on the whole grid
 };
 
 enum { kPhExpand = 0, kPhClaim, kPhOwn, kPhLabels, kPhExchange, kPhRedist, kPhWaitNarrow, kPhOther };
@@ -357,8 +368,9 @@ struct Engine {
         accumulate(cnt, key);
     }
 
-    // Levels-only sweep from root. On return: ecc and the min (degree, id) key of the last level.
-    __device__ bool sweep_levels(int root, int& ecc, unsigned long long& last_key) {
+    // Levels-only sweep from root. On return: ecc, the min (degree, id) key of the last level and
+    // the number of vertices reached (the component's size).
+    __device__ bool sweep_levels(int root, int& ecc, unsigned long long& last_key, long long& reached) {
         Ctl* c = a->ctl;
         const int s = ++sweep_id;
         const int b = cta_rank(), B = cta_count();
@@ -374,6 +386,7 @@ struct Engine {
         int F = 1;
         bool in_cache = true;  // CTA 0's shared cache holds the frontier (narrow runs only)
         ecc = 0;
+        reached = 1;
         if (!kCtaOnly && a->narrow_thr <= 1) {
             if (!barrier()) return false;
             in_cache = false;
@@ -408,6 +421,7 @@ struct Engine {
                         int* t = cur; cur = nxt; nxt = t;
                         cb ^= 1;
                         F = cnt;
+                        reached += cnt;
                         ++ecc;
                         if (!kCtaOnly && F >= a->narrow_thr) break;
                     }
@@ -421,6 +435,7 @@ struct Engine {
                         c->pub_cur = (cur == a->qb) ? 1 : 0;
                         c->pub_ecc = ecc;
                         c->pub_key = lk;
+                        c->pub_reached = reached;
                         c->qtail[ecc % 3] = 0;
                     }
                 }
@@ -437,6 +452,7 @@ struct Engine {
                 const int Fp = sm->bc[0], pc = sm->bc[1];
                 ecc = sm->bc[2];
                 lk = sm->bck;
+                reached = __ldcg(&c->pub_reached);
                 __syncthreads();
                 cur = pc ? a->qb : a->qa;
                 nxt = pc ? a->qa : a->qb;
@@ -464,6 +480,7 @@ struct Engine {
             }
             int* t = cur; cur = nxt; nxt = t;
             F = r.total;
+            reached += r.total;
             ++ecc;
             in_cache = false;
         }
@@ -883,7 +900,188 @@ struct Engine {
         return true;
     }
 
-    // The whole ordering of this graph. Returns false on a failed wait or guard.
+    // One connected component: sweeps from its start vertex r (Alg. 2), labelled traversal
+    // (Alg. 3) with labels from nv. On return, size = the component's vertex count. With
+    // all_left >= 0 (the number of vertices not yet numbered), the call stops after the first
+    // sweep when the component is smaller than that, returning size = -1 (nothing numbered).
+    __device__ bool component(int r, int nv, int& size, long long all_left = -1) {
+        int ecc_prev;
+        unsigned long long k1;
+        long long reached;
+        if (!sweep_levels(r, ecc_prev, k1, reached)) return false;
+        if (all_left >= 0 && reached < all_left) {
+            size = -1;
+            return true;
+        }
+        stat_add(kStSweeps, 1);
+        stat_add(kStTraversals, 1);
+        stat_add(kStLevels, ecc_prev + 1);
+        r = (int)(unsigned)(k1 & 0xffffffffu);
+        int ecc_root = 0;
+        size = 0;
+        if (a->fused) {
+            while (true) {
+                int ecc;
+                unsigned long long k2;
+                if (!sweep_labelled(r, nv, ecc, k2, size)) return false;
+                stat_add(kStSweeps, 1);
+                stat_add(kStTraversals, 1);
+                stat_add(kStLevels, ecc + 1);
+                if (ecc <= ecc_prev) {
+                    ecc_root = ecc;
+                    break;
+                }
+                ecc_prev = ecc;
+                tick(kPhOther);
+                if (!reset_claims(nv, size)) return false;
+                tick(kPhOther);
+                r = (int)(unsigned)(k2 & 0xffffffffu);
+            }
+        } else {
+            while (true) {
+                int ecc;
+                unsigned long long k2;
+                if (!sweep_levels(r, ecc, k2, reached)) return false;
+                stat_add(kStSweeps, 1);
+                stat_add(kStTraversals, 1);
+                stat_add(kStLevels, ecc + 1);
+                if (ecc <= ecc_prev) break;
+                ecc_prev = ecc;
+                r = (int)(unsigned)(k2 & 0xffffffffu);
+            }
+            unsigned long long k2;
+            if (!sweep_labelled(r, nv, ecc_root, k2, size)) return false;
+            stat_add(kStTraversals, 1);
+            stat_add(kStLevels, ecc_root + 1);
+        }
+        stat_add(kStComponents, 1);
+        stat_max(kStMaxEcc, ecc_root);
+        if (size <= 0) {
+            fail(kErrInternal);
+            return false;
+        }
+        return true;
+    }
+
+    // ---------------- concurrent components (whole-grid executor) ----------------
+    // Finds the components still unnumbered after labels [0, nv) and writes the component table
+    // cc_tab (sorted by start key, label offsets from nv; see rcm_cc.cuh). Returns the number of
+    // components, -1 when there are more than cc_cap (the caller continues one by one), -2 on a
+    // failed wait. sort_smem: kCompSmem keys + kCompSmem ints of dynamic shared memory.
+    __device__ int cc_prepare(int nv, unsigned long long* sort_smem) {
+        const int n = a->n;
+        Ctl* c = a->ctl;
+        const int stride = gridDim.x * blockDim.x;
+        const int first = blockIdx.x * blockDim.x + threadIdx.x;
+        for (int v = first; v < n; v += stride) {
+            if (__ldcg(a->claim + v) == kClaimNone) {
+                a->cc_parent[v] = v;
+                a->cc_size[v] = 0;
+                a->cc_key[v] = kKeyMax;
+            }
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) c->ncomp = 0;
+        if (!barrier()) return -2;
+        for (int v = first; v < n; v += stride) {
+            if (__ldcg(a->claim + v) != kClaimNone) continue;
+            int r[8];
+            load_row(v, r);
+            const int d = r[7];
+#pragma unroll
+            for (int k = 0; k < kEllNb; ++k)
+                if (k < d && r[k] < v) cc_union(a->cc_parent, v, r[k]);
+            if (d > kEllNb) {
+                const int rp = __ldg(a->rowptr + v);
+                for (int k = kEllNb; k < d; ++k) {
+                    const int w = __ldg(a->adj + rp + k);
+                    if (w < v) cc_union(a->cc_parent, v, w);
+                }
+            }
+        }
+        if (!barrier()) return -2;
+        for (int v = first; v < n; v += stride) {
+            if (__ldcg(a->claim + v) != kClaimNone) continue;
+            const int r = cc_root((volatile int*)a->cc_parent, v);
+            if (r == v) {
+                const int i = atomicAdd(&c->ncomp, 1);
+                if (i < a->cc_cap) a->cc_roots[i] = v;
+            }
+        }
+        if (!barrier()) return -2;
+        if (threadIdx.x == 0) sm->bc[0] = ldcg(&c->ncomp);
+        __syncthreads();
+        const int C = sm->bc[0];
+        __syncthreads();
+        if (C > a->cc_cap) return -1;
+        // sizes and start keys per root (lanes with the same root combine first)
+        const int lane = threadIdx.x & 31;
+        for (int v0 = blockIdx.x * blockDim.x; v0 < n; v0 += stride) {
+            const int v = v0 + (int)threadIdx.x;
+            const bool ok = v < n && __ldcg(a->claim + v) == kClaimNone;
+            const int root = ok ? cc_root((volatile int*)a->cc_parent, v) : -1;
+            unsigned long long key = ok ? pack_key(__ldg(a->deg + v), v) : kKeyMax;
+            const unsigned grp = __match_any_sync(0xffffffffu, root);
+            unsigned m = grp;
+            while (m) {
+                const int src = __ffs(m) - 1;
+                m &= m - 1;
+                const unsigned long long k2 = __shfl_sync(grp, key, src);
+                key = k2 < key ? k2 : key;
+            }
+            if (ok && lane == __ffs(grp) - 1) {
+                atomicAdd(&a->cc_size[root], __popc(grp));
+                atomicMin(&a->cc_key[root], key);
+            }
+        }
+        if (!barrier()) return -2;
+        // CTA 0: sort by key, label offsets from nv
+        if (blockIdx.x == 0) {
+            int P = 1;
+            while (P < C) P <<= 1;
+            unsigned long long* sk = P <= kCompSmem ? sort_smem : a->cc_gkey;
+            int* si = P <= kCompSmem ? (int*)(sort_smem + kCompSmem) : a->cc_gidx;
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                sk[i] = i < C ? __ldcg(a->cc_key + a->cc_roots[i]) : kKeyMax;
+                si[i] = i < C ? i : 0;
+            }
+            __syncthreads();
+            for (int k = 2; k <= P; k <<= 1) {
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                        const int ixj = i ^ j;
+                        if (ixj > i) {
+                            const bool asc = (i & k) == 0;
+                            const unsigned long long x = sk[i], y = sk[ixj];
+                            if ((x > y) == asc) {
+                                sk[i] = y;
+                                sk[ixj] = x;
+                                const int t = si[i];
+                                si[i] = si[ixj];
+                                si[ixj] = t;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            int carry = nv;
+            for (int i0 = 0; i0 < C; i0 += blockDim.x) {
+                const int i = i0 + (int)threadIdx.x;
+                const int root = i < C ? a->cc_roots[si[i]] : 0;
+                const int sz = i < C ? ldcg(a->cc_size + root) : 0;
+                int tot;
+                const int ex = cta_scan(sz, &tot);
+                if (i < C) a->cc_tab[i] = make_int4((int)(unsigned)(sk[i] & 0xffffffffu), carry + ex, sz, root);
+                carry += tot;
+            }
+            if (threadIdx.x == 0 && carry != n) fail(kErrInternal);
+        }
+        if (!barrier()) return -2;
+        return C;
+    }
+
+    // The whole ordering of this graph, one component after another in start-rule order.
+    // Returns false on a failed wait or guard.
     __device__ bool run() {
         const int n = a->n;
         int Z = 0;
@@ -900,56 +1098,8 @@ struct Engine {
                 fail(kErrInternal);
                 return false;
             }
-            stat_add(kStComponents, 1);
-            int r = (int)(unsigned)(k0 & 0xffffffffu);
-            int ecc_prev;
-            unsigned long long k1;
-            if (!sweep_levels(r, ecc_prev, k1)) return false;
-            stat_add(kStSweeps, 1);
-            stat_add(kStTraversals, 1);
-            stat_add(kStLevels, ecc_prev + 1);
-            r = (int)(unsigned)(k1 & 0xffffffffu);
-            int size = 0, ecc_root = 0;
-            if (a->fused) {
-                while (true) {
-                    int ecc;
-                    unsigned long long k2;
-                    if (!sweep_labelled(r, nv, ecc, k2, size)) return false;
-                    stat_add(kStSweeps, 1);
-                    stat_add(kStTraversals, 1);
-                    stat_add(kStLevels, ecc + 1);
-                    if (ecc <= ecc_prev) {
-                        ecc_root = ecc;
-                        break;
-                    }
-                    ecc_prev = ecc;
-                    tick(kPhOther);
-                    if (!reset_claims(nv, size)) return false;
-                    tick(kPhOther);
-                    r = (int)(unsigned)(k2 & 0xffffffffu);
-                }
-            } else {
-                while (true) {
-                    int ecc;
-                    unsigned long long k2;
-                    if (!sweep_levels(r, ecc, k2)) return false;
-                    stat_add(kStSweeps, 1);
-                    stat_add(kStTraversals, 1);
-                    stat_add(kStLevels, ecc + 1);
-                    if (ecc <= ecc_prev) break;
-                    ecc_prev = ecc;
-                    r = (int)(unsigned)(k2 & 0xffffffffu);
-                }
-                unsigned long long k2;
-                if (!sweep_labelled(r, nv, ecc_root, k2, size)) return false;
-                stat_add(kStTraversals, 1);
-                stat_add(kStLevels, ecc_root + 1);
-            }
-            stat_max(kStMaxEcc, ecc_root);
-            if (size <= 0) {
-                fail(kErrInternal);
-                return false;
-            }
+            int size;
+            if (!component((int)(unsigned)(k0 & 0xffffffffu), nv, size)) return false;
             nv += size;
         }
         return true;

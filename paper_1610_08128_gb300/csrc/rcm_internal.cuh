@@ -38,6 +38,7 @@ struct alignas(128) Ctl {
     int nbig;              // rows longer than the per-thread sorter handles
     int work_next;         // next work item of a dynamic queue (batched engine)
     int qtail[3];          // ring of queue / staging tails, indexed by level
+    int ncomp;             // connected components (counted before the traversal)
     unsigned int arrive;   // monotone arrival counter of the grid exchange
     // state published by CTA 0 at the end of a run of narrow levels
     int pub_F;       // current frontier size (0 = traversal finished)
@@ -47,6 +48,7 @@ struct alignas(128) Ctl {
     int pub_lastF;   // size of the last non-empty level when finished
     int pub_pad[3];
     unsigned long long pub_key;    // min (degree, id) key of the last level when finished
+    long long pub_reached;         // vertices reached so far (levels-only sweeps)
     long long stats[8];            // rcm_stats fields, in order
     long long phase_ns[8];         // per-phase time of CTA 0 (profile_phases)
     ExSlot slots[2][kMaxGridBlocks];  // exchange slots, double-buffered by epoch parity

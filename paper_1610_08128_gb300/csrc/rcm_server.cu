@@ -101,6 +101,11 @@ __global__ void __launch_bounds__(kReqThreads, 2) k_rcm_request(ReqDesc r) {
     a.obits = claim_order_bits(n);
     a.profile = 0;
     a.limit_ns = 0;
+    a.cc_parent = a.cc_size = a.cc_roots = a.cc_gidx = nullptr;
+    a.cc_key = a.cc_gkey = nullptr;
+    a.cc_tab = nullptr;
+    a.cc_cap = 0;
+    a.cc_big = 0;
     Engine<true> e;
     e.init(a, &smem);
     e.run();

@@ -14,13 +14,107 @@ namespace rcm {
 template <int kThreads>
 __global__ void __launch_bounds__(kThreads, 1) k_rcm_single(EngineArgs args, int stall) {
     __shared__ EngineSmem smem;
-    if (ld_volatile(&args.ctl->status) & kErrBadCsr) return;
+    __shared__ int s_item;
+    extern __shared__ unsigned long long s_sort[];  // component-table sort (kCompSmem entries)
+    Ctl* ctl = args.ctl;
+    if (ld_volatile(&ctl->status) & kErrBadCsr) return;
     if (stall && blockIdx.x == 0) return;  // test hook: the other CTAs' first wait runs out
+    const int n = args.n;
     Engine<false> e;
     e.init(args, &smem);
-    if (e.run() && blockIdx.x == 0 && threadIdx.x == 0) {
-        for (int i = 0; i < 8; ++i) args.ctl->stats[i] = smem.st[i];
-        for (int i = 0; i < 8; ++i) args.ctl->phase_ns[i] = smem.prof[i];
+    int Z = 0;
+    if (!e.label_isolated(Z)) return;
+    e.stat_add(kStIsolated, Z);
+    e.stat_add(kStComponents, Z);
+    int nv = Z;
+    int C = -1;
+    bool first = true, tried = false;
+    while (nv < n) {
+        if (!first && !tried && args.cc_cap > 0) {
+            // more than one component: order them concurrently (one attempt)
+            tried = true;
+            C = e.cc_prepare(nv, s_sort);
+            if (C == -2) return;
+            if (C > 0) break;
+        }
+        unsigned long long k0;
+        if (!e.next_start(k0)) return;
+        if (k0 == kKeyMax) {
+            e.fail(kErrInternal);
+            return;
+        }
+        int size;
+        // the first component's first sweep shows whether it spans everything left
+        const long long left = (first && args.cc_cap > 0) ? (long long)(n - nv) : -1;
+        first = false;
+        if (!e.component((int)(unsigned)(k0 & 0xffffffffu), nv, size, left)) return;
+        if (size < 0) continue;  // more components: the next iteration prepares them all
+        nv += size;
+    }
+    if (C > 0) {
+        // large components on the whole grid, one after another
+        for (int i = 0; i < C; ++i) {
+            const int4 t = __ldcg(args.cc_tab + i);
+            if (t.z < args.cc_big) continue;
+            int size;
+            if (!e.component(t.x, t.y, size)) return;
+            if (size != t.z) {
+                e.fail(kErrInternal);
+                return;
+            }
+        }
+    }
+    // statistics: CTA 0 adds the grid part; CTAs add their own parts below (ctl->stats starts at 0)
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int i = 0; i < 8; ++i) {
+            if (i == kStMaxEcc) atomicMax((unsigned long long*)&ctl->stats[i], (unsigned long long)smem.st[i]);
+            else atomicAdd((unsigned long long*)&ctl->stats[i], (unsigned long long)smem.st[i]);
+        }
+        for (int i = 0; i < 8; ++i) ctl->phase_ns[i] = smem.prof[i];
+    }
+    if (C <= 0) return;
+    // the other components, one per CTA (CTA barriers only)
+    __syncthreads();
+    Engine<true> ec;
+    bool any = false;
+    while (true) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&ctl->work_next, 1);
+        __syncthreads();
+        const int i = s_item;
+        __syncthreads();
+        if (i >= C) break;
+        const int4 t = __ldcg(args.cc_tab + i);
+        if (t.z >= args.cc_big) continue;
+        EngineArgs ca = args;
+        ca.qa = args.qa + t.y;
+        ca.qb = args.qb + t.y;
+        ca.boff = args.boff + t.y;
+        ca.narrow_thr = 0x7fffffff;
+        ca.obits = claim_order_bits(t.z);
+        ca.profile = 0;
+        if (!any) {
+            ec.init(ca, &smem);
+            // visit stamps of these engines stay clear of the grid engine's (whose first sweep may
+            // already have stamped the first component)
+            ec.sweep_id = 1 << 24;
+            any = true;
+        } else {
+            __syncthreads();
+            if (threadIdx.x == 0) smem.args = ca;
+            __syncthreads();
+        }
+        int size;
+        if (!ec.component(t.x, t.y, size)) return;
+        if (size != t.z) {
+            ec.fail(kErrInternal);
+            return;
+        }
+    }
+    if (any && threadIdx.x == 0) {
+        for (int i = 0; i < 8; ++i) {
+            if (i == kStMaxEcc) atomicMax((unsigned long long*)&ctl->stats[i], (unsigned long long)smem.st[i]);
+            else if (i != kStIsolated && i != kStGrid) atomicAdd((unsigned long long*)&ctl->stats[i], (unsigned long long)smem.st[i]);
+        }
     }
 }
 
@@ -33,11 +127,18 @@ __global__ void k_init_ctl(Ctl* ctl, int nnz, const int* rowptr_n) {
 // ------------------------------------------------------------------------------------------
 // host side
 
+// Components of at least this many vertices are ordered by the whole grid; smaller ones by one
+// CTA each, concurrently.
+constexpr int kComponentOnGrid = 1 << 18;
+
 struct SingleLayout {
-    size_t ctl, pool4, deg, claim, vis, bigrows, adj, ell, total;
+    size_t ctl, pool4, deg, claim, vis, bigrows, adj, ell, cc_size, cc_key, cc_roots, cc_gkey, cc_gidx, cc_tab, total;
+    int cc_cap;
 };
 
-static SingleLayout single_layout(long long n, long long nnz) {
+// with_cc: also the arrays of the concurrent-components pass (the fixed no-allocation workspace
+// leaves them out and orders components one by one).
+static SingleLayout single_layout(long long n, long long nnz, bool with_cc = true) {
     SingleLayout L;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -53,6 +154,20 @@ static SingleLayout single_layout(long long n, long long nnz) {
     L.bigrows = take(sizeof(int) * (size_t)std::max(n, 1LL));
     L.adj = take(sizeof(int) * (size_t)std::max(nnz, 1LL));
     L.ell = take(sizeof(int4) * 2 * (size_t)std::max(n, 1LL));
+    L.cc_cap = with_cc ? (int)std::min<long long>(std::max(n, 1LL), kMaxComps) : 0;
+    if (!with_cc) {
+        L.cc_size = L.cc_key = L.cc_roots = L.cc_gkey = L.cc_gidx = L.cc_tab = 0;
+        L.total = o;
+        return L;
+    }
+    long long cap2 = 1;
+    while (cap2 < L.cc_cap) cap2 <<= 1;
+    L.cc_size = take(sizeof(int) * (size_t)std::max(n, 1LL));
+    L.cc_key = take(sizeof(unsigned long long) * (size_t)std::max(n, 1LL));
+    L.cc_roots = take(sizeof(int) * (size_t)L.cc_cap);
+    L.cc_gkey = take(sizeof(unsigned long long) * (size_t)cap2);
+    L.cc_gidx = take(sizeof(int) * (size_t)cap2);
+    L.cc_tab = take(sizeof(int4) * (size_t)L.cc_cap);
     L.total = o;
     return L;
 }
@@ -83,12 +198,15 @@ static const void* single_kernel(int threads) {
     return (const void*)k_rcm_single<512>;
 }
 
+constexpr int kSingleDynSmem = (int)((sizeof(unsigned long long) + sizeof(int)) * kCompSmem);
+
 static int single_blocks_per_sm(int threads) {
     std::lock_guard<std::mutex> g(g_single_mu);
     const int idx = threads_index(threads);
     if (g_single_blocks_per_sm[idx] < 0) {
         int b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, single_kernel(threads), threads, 0);
+        cudaFuncSetAttribute(single_kernel(threads), cudaFuncAttributeMaxDynamicSharedMemorySize, kSingleDynSmem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, single_kernel(threads), threads, kSingleDynSmem);
         g_single_blocks_per_sm[idx] = b;
         cudaFuncSetAttribute(k_sort_rows_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(unsigned long long) * kBigRowSmem));
@@ -167,11 +285,20 @@ rcm_status order_single(int32_t n, int64_t nnz, const int32_t* rowptr, const int
         args.narrow_thr = narrow;
         args.obits = obits;
         args.profile = o.profile_phases ? 1 : 0;
+        args.cc_parent = pool4 + 3 * (size_t)n;
+        args.cc_size = (int*)(base + L.cc_size);
+        args.cc_key = (unsigned long long*)(base + L.cc_key);
+        args.cc_roots = (int*)(base + L.cc_roots);
+        args.cc_gkey = (unsigned long long*)(base + L.cc_gkey);
+        args.cc_gidx = (int*)(base + L.cc_gidx);
+        args.cc_tab = (int4*)(base + L.cc_tab);
+        args.cc_cap = L.cc_cap;
+        args.cc_big = kComponentOnGrid;
         args.fused = o.fused_sweeps >= 0 ? 1 : 0;
         args.limit_ns = limit;
         int stall = o.debug_stall_barrier ? 1 : 0;
         void* kargs[] = {&args, &stall};
-        e = cudaLaunchCooperativeKernel(single_kernel(threads), dim3(blocks), dim3(threads), kargs, 0, s);
+        e = cudaLaunchCooperativeKernel(single_kernel(threads), dim3(blocks), dim3(threads), kargs, kSingleDynSmem, s);
         if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
     }
     if (e == cudaSuccess) e = enqueue_latch(ctl, stream_latch(s), stats_dev, s);
@@ -245,7 +372,7 @@ rcm_status order_single_noalloc(int32_t n, const int32_t* rowptr, const int32_t*
     if (nnz < 0) return RCM_ERR_BAD_CSR;
     if (nnz > kNoAllocMaxNnz) return RCM_ERR_TOO_LARGE;
     if (nnz > 0 && !colidx) return RCM_ERR_INVALID_ARG;
-    const SingleLayout L = single_layout(n, nnz);
+    const SingleLayout L = single_layout(n, nnz, false);
     if (L.total > kNoAllocBytes) return RCM_ERR_TOO_LARGE;
 
     const DeviceInfo& di = device_info();
@@ -301,9 +428,14 @@ rcm_status order_single_noalloc(int32_t n, const int32_t* rowptr, const int32_t*
         args.profile = 0;
         args.fused = 1;
         args.limit_ns = 20000000000LL;
+        args.cc_parent = args.cc_size = args.cc_roots = args.cc_gidx = nullptr;
+        args.cc_key = args.cc_gkey = nullptr;
+        args.cc_tab = nullptr;
+        args.cc_cap = 0;
+        args.cc_big = 0;
         int stall = 0;
         void* kargs[] = {&args, &stall};
-        e = cudaLaunchCooperativeKernel(single_kernel(threads), dim3(blocks), dim3(threads), kargs, 0, s);
+        e = cudaLaunchCooperativeKernel(single_kernel(threads), dim3(blocks), dim3(threads), kargs, kSingleDynSmem, s);
     }
     // synchronous: the device-detected status is read back from the control block
     int bits = 0;

@@ -127,6 +127,19 @@ def test_meshes():
     assert_parity(synth.knn_mesh(30000, 3, 11))
 
 
+def test_components_concurrent_with_a_grid_sized_one():
+    """One component large enough for the whole grid plus thousands of small ones (run one per
+    CTA), and the same with isolated vertices: labels still follow the start rule exactly."""
+    big = synth.grid((600, 520), seed=61)                       # 312,000 vertices, one component
+    small = synth.random_graph(40000, 30000, 62)                # thousands of small components
+    g = synth.concat([big, small])
+    merged = synth.Csr(g.n, g.rowptr, g.colidx)
+    p = synth.random_permutation(g.n, 63)
+    assert_parity(synth.permute(merged, p))
+    g2 = synth.concat([small, synth.csr_from_edges(500, [], []), big])
+    assert_parity(synth.permute(synth.Csr(g2.n, g2.rowptr, g2.colidx), synth.random_permutation(g2.n, 64)))
+
+
 OPTION_SETS = [
     {"narrow_threshold": -1},            # whole grid for every level
     {"narrow_threshold": 1 << 30},       # CTA 0 for every level
