@@ -43,6 +43,12 @@ def parse_args():
     p.add_argument("--cpu-samples", type=int, default=3)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-served", action="store_true")
+    p.add_argument("--batch-graphs", type=int, default=10_000)
+    p.add_argument("--serve-requests", type=int, default=1000)
+    p.add_argument("--serve-pool", type=int, default=32)
+    p.add_argument("--serve-rate", type=float, default=2000.0)
     return p.parse_args()
 
 
@@ -156,6 +162,125 @@ def make_workload(side: int):
                "n": g.n, "nnz": g.nnz}
 
 
+def pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))] if xs else None
+
+
+def bench_batched(args, torch, rcm, synth, workers):
+    """10,000 graphs (log-uniform 100..50,000 vertices; 2D grid / 3D grid / kNN(3) mesh) ordered by
+    one rcm_order_batch call, against one rcm_order call per graph (sampled)."""
+    import numpy as np
+
+    b = synth.c4_batch(G=args.batch_graphs, workers=workers)
+    goff = torch.from_numpy(b.goff).cuda()
+    rp = torch.from_numpy(b.rowptr).cuda()
+    ci = torch.from_numpy(b.colidx).cuda()
+    perm = torch.empty(b.n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def once():
+        rcm.check(rcm.rcm_order_batch(b.G, b.n, goff, rp, ci, perm, stream), "rcm_order_batch")
+        rcm.check(rcm.rcm_stream_status(stream), "rcm_order_batch")
+
+    once()
+    times = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        once()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    t = statistics.median(times)
+    # plain path: one rcm_order per graph on a sample, inputs already on the device
+    rng = synth.rng_for(7)
+    sample = rng.choice(b.G, min(200, b.G), replace=False)
+    dev = []
+    for gi in sample:
+        g = b.graphs[gi]
+        dev.append((g, torch.from_numpy(g.rowptr).cuda(), torch.from_numpy(g.colidx if g.nnz else np.zeros(1, np.int32)).cuda(),
+                    torch.empty(max(g.n, 1), dtype=torch.int32, device="cuda")))
+    opts = rcm.rcm_options()
+    for g, r, c, pm in dev[:5]:
+        opts.nnz = g.nnz
+        rcm.check(rcm.rcm_order_ex(g.n, r, c, pm, opts, None, stream), "plain")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for g, r, c, pm in dev:
+        opts.nnz = g.nnz
+        rcm.check(rcm.rcm_order_ex(g.n, r, c, pm, opts, None, stream), "plain")
+    rcm.check(rcm.rcm_stream_status(stream), "plain")
+    t_plain = (time.perf_counter() - t0) / len(dev)
+    # bit-exact spot check: batch segment == plain result on the sample
+    host = perm.cpu().numpy()
+    same = all(np.array_equal(host[b.goff[gi]:b.goff[gi + 1]], pm.cpu().numpy()[:b.graphs[gi].n])
+               for gi, (_, _, _, pm) in zip(sample, dev))
+    return {"workload": f"{b.G} graphs, n log-uniform 100..50,000, 2D grid / 3D grid / kNN(3) mesh",
+            "vertices": b.n, "entries": int(b.rowptr[-1]), "ms": t * 1e3, "orderings_per_s": b.G / t,
+            "plain_orderings_per_s": 1.0 / t_plain, "plain_sample": len(dev), "vs_plain": (b.G / t) * t_plain,
+            "sample_equal_to_plain": bool(same), "gpu_launches": 5}
+
+
+def bench_served(args, torch, rcm, synth, workers):
+    """Poisson request stream replayed through the server (continuous batching), against the same
+    trace served FIFO by rcm_order_host (simulated from measured per-graph service times)."""
+    import numpy as np
+
+    arrival, which, pool = synth.c5_trace(requests=args.serve_requests, rate_per_s=args.serve_rate,
+                                          pool=args.serve_pool, workers=workers)
+    bufs = []
+    for g in pool:
+        bufs.append((torch.from_numpy(g.rowptr).pin_memory(), torch.from_numpy(g.colidx).pin_memory()))
+    # FIFO baseline service times through the plain host API
+    service = []
+    for g, (r, c) in zip(pool, bufs):
+        out = torch.empty(g.n, dtype=torch.int32).pin_memory()
+        rcm.check(rcm.rcm_order_host(g.n, r, c, out), "plain")
+        t0 = time.perf_counter()
+        rcm.check(rcm.rcm_order_host(g.n, r, c, out), "plain")
+        service.append(time.perf_counter() - t0)
+    fin, lat = 0.0, []
+    for t_a, gi in zip(arrival, which):
+        fin = max(fin, t_a) + service[gi]
+        lat.append(fin - t_a)
+    fifo_rate = len(arrival) / fin
+    # served
+    st, srv = rcm.rcm_server_create(60 << 30, 256)
+    rcm.check(st, "rcm_server_create")
+    outs = [torch.empty(pool[gi].n, dtype=torch.int32).pin_memory() for gi in which]
+    tickets = []
+    t_start = time.perf_counter()
+    for k, (t_a, gi) in enumerate(zip(arrival, which)):
+        while time.perf_counter() - t_start < t_a:
+            pass
+        g = pool[gi]
+        s, t = rcm.rcm_submit(srv, g.n, g.nnz, bufs[gi][0], bufs[gi][1], outs[k])
+        rcm.check(s, "rcm_submit")
+        tickets.append(t)
+    for t in tickets:
+        rcm.check(rcm.rcm_wait(srv, t), "rcm_wait")
+    t_total = time.perf_counter() - t_start
+    _, info = rcm.rcm_server_info(srv)
+    rcm.rcm_server_destroy(srv)
+    # results served in the mix equal the plain path's
+    same = True
+    for k in range(0, len(which), max(1, len(which) // 16)):
+        g = pool[which[k]]
+        ref = torch.empty(g.n, dtype=torch.int32).pin_memory()
+        rcm.check(rcm.rcm_order_host(g.n, bufs[which[k]][0], bufs[which[k]][1], ref), "plain")
+        same &= bool(torch.equal(ref, outs[k]))
+    sizes = [pool[gi].n for gi in which]
+    return {"workload": f"{len(arrival)} requests, Poisson {args.serve_rate:.0f}/s, pool of {len(pool)} graphs "
+                        f"(n log-uniform 1e3..4e6, 3 generators), 60 GB budget",
+            "mean_vertices": float(np.mean(sizes)), "orderings_per_s": len(arrival) / t_total,
+            "p50_ms": info["latency_p50_s"] * 1e3, "p99_ms": info["latency_p99_s"] * 1e3,
+            "max_concurrent": info["max_running"], "arena_peak_gb": info["arena_peak_bytes"] / 1e9,
+            "fifo_plain_orderings_per_s": fifo_rate, "fifo_plain_p50_ms": pct(lat, 0.5) * 1e3,
+            "fifo_plain_p99_ms": pct(lat, 0.99) * 1e3, "vs_fifo_plain": (len(arrival) / t_total) / fifo_rate,
+            "served_equal_to_plain": same}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -205,7 +330,9 @@ def main():
 
     from paper_1610_08128_gb300 import build as b
     from paper_1610_08128_gb300 import rcm
+    from paper_1610_08128_gb300 import synth as synth_mod
 
+    workers = synth_mod.default_workers()
     b.build()
     rcm.load()
     g, cfg = make_workload(args.side)
@@ -303,6 +430,12 @@ def main():
                "sample": f"{args.cpu_samples} serial orderings of the full workload",
                "ms_per_ordering": statistics.mean(ts) * 1e3}
 
+    batched = served = None
+    if rank == 0 and not args.no_batched:
+        batched = bench_batched(args, torch, rcm, synth_mod, workers)
+    if rank == 0 and not args.no_served:
+        served = bench_served(args, torch, rcm, synth_mod, workers)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -314,6 +447,7 @@ def main():
             "gpu_launches": 6 * args.steps, "clocks": clocks,
             "stats": dict(stats, prep_ms=statistics.mean(prep_ms), traverse_ms=trav),
             "quality": {"bandwidth": bw, "profile": prof},
+            "batched": batched, "served": served,
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -171,9 +171,10 @@ rcm_status rcm_order_noalloc(int32_t n, const int32_t *rowptr, const int32_t *co
  * A server owns a device arena of hbm_budget_bytes (allocated once at creation) and up to
  * max_inflight concurrent requests. Each request needs one arena region: its CSR when given in
  * host memory, its output when the caller's buffer is in host memory, and the ordering's
- * workspace (about 68 bytes per vertex plus 4 bytes per stored entry). Requests are admitted in
- * arrival order as regions and slots free up; each admitted request runs on its own stream as a
- * single-CTA kernel, so requests that arrive while others are on the GPU run alongside them.
+ * workspace (rcm_request_bytes gives the exact size). Requests are admitted in
+ * arrival order as regions and slots free up; each admitted request runs on its own stream (its
+ * validation and sorted-row kernels, then one CTA of the batched executor), so requests that
+ * arrive while others are on the GPU run alongside them.
  * Results are bit-identical to rcm_order on the same pattern.
  */
 typedef struct rcm_server rcm_server;
@@ -189,6 +190,14 @@ typedef struct {
     double latency_p99_s;
     double latency_max_s;
 } rcm_server_stats;
+
+/*
+ * Arena bytes one request of n vertices and nnz stored entries takes: the staged CSR when
+ * host_csr != 0 (rowptr/colidx in host memory), the staged result when host_out != 0, a status
+ * block, and the ordering's workspace (about 124 bytes per vertex, 4 per stored entry and 34 KB).
+ * A budget of at least this many bytes admits the request. Pure host arithmetic.
+ */
+size_t rcm_request_bytes(int32_t n, int64_t nnz, int32_t host_csr, int32_t host_out);
 
 /* Creates a server on the current device. max_inflight in [1, 4096]. */
 rcm_status rcm_server_create(size_t hbm_budget_bytes, int32_t max_inflight, rcm_server **out);

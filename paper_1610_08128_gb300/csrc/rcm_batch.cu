@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <mutex>
 
+#include "rcm_batch.cuh"
+#include "rcm_cc.cuh"
 #include "rcm_engine.cuh"
 #include "rcm_host.hpp"
 #include "rcm_internal.cuh"
@@ -29,33 +31,25 @@ __global__ void k_batch_validate(int G, int n_total, const long long* __restrict
             if (goff[mid] <= v) lo = mid; else hi = mid - 1;
         }
         const long long a = goff[lo], b = goff[lo + 1];
-        for (int k = rowptr[v]; k < rowptr[v + 1]; ++k) {
+        const int r0 = rowptr[v], r1 = rowptr[v + 1];
+        if (r0 < 0 || r1 < r0 || r1 > rowptr[n_total]) {
+            atomicOr(&ctl->status, kErrBadCsr);
+            continue;
+        }
+        for (int k = r0; k < r1; ++k) {
             const int w = colidx[k];
             if (w < a || w >= b) atomicOr(&ctl->status, kErrBadCsr);
         }
     }
 }
 
-struct BatchArgs {
-    int G;
-    const long long* goff;
-    const int* rowptr;
-    const int4* ell;
-    const int* adj;
-    const int* deg;
-    unsigned long long* claim;
-    int* vis;
-    int* qa;
-    int* qb;
-    int* boff;
-    int* perm;
-    Ctl* ctl;
-};
+constexpr int kBatchSortCap = 2048;  // component tables sorted in shared memory up to this size
 
 template <int kThreads>
 __global__ void __launch_bounds__(kThreads) k_rcm_batch(BatchArgs b) {
     __shared__ EngineSmem smem;
     __shared__ int s_item;
+    __shared__ unsigned long long s_sort[kBatchSortCap + kBatchSortCap / 2];
     if (ld_volatile(&b.ctl->status) & kErrBadCsr) return;
     Engine<true> e;
     while (true) {
@@ -82,18 +76,25 @@ __global__ void __launch_bounds__(kThreads) k_rcm_batch(BatchArgs b) {
         a.perm = b.perm + v0;
         a.ctl = b.ctl;
         a.status = &b.ctl->status;
+        a.diag = nullptr;
         a.narrow_thr = 0x7fffffff;
         a.obits = claim_order_bits(n);
         a.profile = 0;
-        a.cc_parent = a.cc_size = a.cc_roots = a.cc_gidx = nullptr;
-        a.cc_key = a.cc_gkey = nullptr;
-        a.cc_tab = nullptr;
-        a.cc_cap = 0;
+        a.cc_parent = b.cc_parent;
+        a.cc_size = b.cc_size;
+        a.cc_key = b.cc_key;
+        a.cc_roots = b.cc_roots + v0;
+        a.cc_gkey = b.cc_gkey + 2 * (size_t)v0;
+        a.cc_gidx = b.cc_gidx + 2 * (size_t)v0;
+        a.cc_tab = b.cc_tab + v0;
+        a.cc_cap = n;
         a.cc_big = 0;
         a.fused = 1;
         a.limit_ns = 0;
         __syncthreads();
         e.init(a, &smem);
+        e.sm_sort = s_sort;
+        e.sm_sort_cap = kBatchSortCap;
         if (!e.run()) return;
         __syncthreads();
         // the segment holds global ids while running; the result is in local ids
@@ -102,85 +103,115 @@ __global__ void __launch_bounds__(kThreads) k_rcm_batch(BatchArgs b) {
     }
 }
 
+BatchLayout batch_layout(long long n_total, long long nnz) {
+    const size_t N = (size_t)std::max<long long>(n_total, 1), E = (size_t)std::max<long long>(nnz, 1);
+    BatchLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + bytes, 256);
+        return at;
+    };
+    L.ctl = take(sizeof(Ctl));
+    L.pool = take(sizeof(int) * 4 * N);
+    L.deg = take(sizeof(int) * N);
+    L.claim = take(sizeof(unsigned long long) * N);
+    L.vis = take(sizeof(int) * N);
+    L.big = take(sizeof(int) * N);
+    L.adj = take(sizeof(int) * E);
+    L.ell = take(sizeof(int4) * 2 * N);
+    L.ccs = take(sizeof(int) * N);
+    L.cck = take(sizeof(unsigned long long) * N);
+    L.ccr = take(sizeof(int) * N);
+    L.ccgk = take(sizeof(unsigned long long) * 2 * N);
+    L.ccgi = take(sizeof(int) * 2 * N);
+    L.cct = take(sizeof(int4) * N);
+    L.total = o;
+    return L;
+}
+
 static std::mutex g_batch_mu;
 static int g_batch_per_sm = -1;
 
-rcm_status order_batch(int32_t G, int64_t n_total, const int64_t* goff, const int32_t* rowptr,
-                       const int32_t* colidx, int32_t* perm, cudaStream_t s) {
+static int batch_blocks_per_sm() {
+    std::lock_guard<std::mutex> g(g_batch_mu);
+    if (g_batch_per_sm < 0) {
+        int bps = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_rcm_batch<256>, 256, 0);
+        g_batch_per_sm = bps;
+        cudaFuncSetAttribute(k_sort_rows_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(unsigned long long) * kBigRowSmem));
+    }
+    return g_batch_per_sm;
+}
+
+cudaError_t enqueue_batch(int G, long long n_total, int nnz, const long long* goff, const int* rowptr,
+                          const int* colidx, int* perm, char* base, const BatchLayout& L, cudaStream_t s) {
     constexpr int kThreads = 256;
     const DeviceInfo& di = device_info();
-    {
-        std::lock_guard<std::mutex> g(g_batch_mu);
-        if (g_batch_per_sm < 0) {
-            int bps = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_rcm_batch<kThreads>, kThreads, 0);
-            g_batch_per_sm = bps;
-            cudaFuncSetAttribute(k_sort_rows_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(unsigned long long) * kBigRowSmem));
-        }
-    }
-    if (g_batch_per_sm <= 0) return RCM_ERR_CUDA;
+    const int per_sm = batch_blocks_per_sm();
+    if (per_sm <= 0) return cudaErrorInvalidConfiguration;
+    const long long N = std::max<long long>(n_total, 1);
+    Ctl* ctl = (Ctl*)(base + L.ctl);
+    int* pool4 = (int*)(base + L.pool);
+    int* deg = (int*)(base + L.deg);
+    unsigned long long* claim = (unsigned long long*)(base + L.claim);
+    int* vis = (int*)(base + L.vis);
+    int* big = (int*)(base + L.big);
+    int* adj = (int*)(base + L.adj);
+    int4* ell = (int4*)(base + L.ell);
+    cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), s);
+    if (e != cudaSuccess) return e;
+    const int pb = 256;
+    const int pgrid = (int)std::max<long long>(1, std::min<long long>((n_total + pb - 1) / pb, (long long)di.sms * 16));
+    // rows longer than kSmallRowMax entries number at most nnz / (kSmallRowMax + 1)
+    const int big_grid = (int)std::max<long long>(1, std::min<long long>(2LL * di.sms, nnz / (kSmallRowMax + 1)));
+    if (G > 1) k_batch_validate<<<pgrid, pb, 0, s>>>(G, (int)n_total, goff, rowptr, colidx, ctl);
+    k_degree_validate<<<pgrid, pb, 0, s>>>((int)n_total, nnz, rowptr, colidx, deg, claim, vis, big, ctl, kSmallRowMax);
+    k_sort_rows_small<<<pgrid, pb, 0, s>>>((int)n_total, rowptr, colidx, deg, adj, ell, ctl);
+    k_sort_rows_big<<<big_grid, 1024, sizeof(unsigned long long) * kBigRowSmem, s>>>(
+        (int)n_total, rowptr, colidx, deg, adj, ell, big, ctl, (unsigned long long*)pool4);
+    BatchArgs b;
+    b.G = G;
+    b.goff = goff;
+    b.rowptr = rowptr;
+    b.ell = ell;
+    b.adj = adj;
+    b.deg = deg;
+    b.claim = claim;
+    b.vis = vis;
+    b.qa = pool4;
+    b.qb = pool4 + N;
+    b.boff = pool4 + 2 * N;
+    b.perm = perm;
+    b.ctl = ctl;
+    b.cc_parent = pool4 + 3 * N;
+    b.cc_size = (int*)(base + L.ccs);
+    b.cc_key = (unsigned long long*)(base + L.cck);
+    b.cc_roots = (int*)(base + L.ccr);
+    b.cc_gkey = (unsigned long long*)(base + L.ccgk);
+    b.cc_gidx = (int*)(base + L.ccgi);
+    b.cc_tab = (int4*)(base + L.cct);
+    const int blocks = (int)std::min<long long>((long long)per_sm * di.sms, std::max(G, 1));
+    k_rcm_batch<kThreads><<<blocks, kThreads, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+rcm_status order_batch(int32_t G, int64_t n_total, const int64_t* goff, const int32_t* rowptr,
+                       const int32_t* colidx, int32_t* perm, cudaStream_t s) {
     // nnz is needed to size the sorted-adjacency copy: one 4-byte read, synchronised on s
     int nnz = 0;
     cudaError_t e = cudaMemcpyAsync(&nnz, rowptr + n_total, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_status(e);
     if (nnz < 0) return RCM_ERR_BAD_CSR;
-    const long long N = std::max<long long>(n_total, 1);
-    size_t o = 0;
-    auto take = [&](size_t bytes) {
-        size_t at = o;
-        o = align_up(o + bytes, 256);
-        return at;
-    };
-    const size_t o_ctl = take(sizeof(Ctl));
-    const size_t o_pool = take(sizeof(int) * 4 * (size_t)N);
-    const size_t o_deg = take(sizeof(int) * (size_t)N);
-    const size_t o_claim = take(sizeof(unsigned long long) * (size_t)N);
-    const size_t o_vis = take(sizeof(int) * (size_t)N);
-    const size_t o_big = take(sizeof(int) * (size_t)N);
-    const size_t o_adj = take(sizeof(int) * (size_t)std::max(nnz, 1));
-    const size_t o_ell = take(sizeof(int4) * 2 * (size_t)N);
+    const BatchLayout L = batch_layout(n_total, nnz);
     void* ws = nullptr;
-    rcm_status st = ws_alloc(&ws, o, s);
+    rcm_status st = ws_alloc(&ws, L.total, s);
     if (st != RCM_OK) return st;
     char* base = (char*)ws;
-    Ctl* ctl = (Ctl*)(base + o_ctl);
-    int* pool4 = (int*)(base + o_pool);
-    int* deg = (int*)(base + o_deg);
-    unsigned long long* claim = (unsigned long long*)(base + o_claim);
-    int* vis = (int*)(base + o_vis);
-    int* big = (int*)(base + o_big);
-    int* adj = (int*)(base + o_adj);
-    int4* ell = (int4*)(base + o_ell);
-    e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), s);
-    if (e == cudaSuccess) {
-        const int pb = 256;
-        const int pgrid = (int)std::max<long long>(1, std::min<long long>((n_total + pb - 1) / pb, (long long)di.sms * 16));
-        k_batch_validate<<<pgrid, pb, 0, s>>>(G, (int)n_total, (const long long*)goff, rowptr, colidx, ctl);
-        k_degree_validate<<<pgrid, pb, 0, s>>>((int)n_total, rowptr, colidx, deg, claim, vis, big, ctl, kSmallRowMax);
-        k_sort_rows_small<<<pgrid, pb, 0, s>>>((int)n_total, rowptr, colidx, deg, adj, ell, ctl);
-        k_sort_rows_big<<<di.sms * 2, 1024, sizeof(unsigned long long) * kBigRowSmem, s>>>(
-            (int)n_total, rowptr, colidx, deg, adj, ell, big, ctl, (unsigned long long*)pool4);
-        BatchArgs b;
-        b.G = G;
-        b.goff = (const long long*)goff;
-        b.rowptr = rowptr;
-        b.ell = ell;
-        b.adj = adj;
-        b.deg = deg;
-        b.claim = claim;
-        b.vis = vis;
-        b.qa = pool4;
-        b.qb = pool4 + N;
-        b.boff = pool4 + 2 * N;
-        b.perm = perm;
-        b.ctl = ctl;
-        const int blocks = (int)std::min<long long>((long long)g_batch_per_sm * di.sms, std::max(G, 1));
-        k_rcm_batch<kThreads><<<blocks, kThreads, 0, s>>>(b);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = enqueue_latch(ctl, stream_latch(s), nullptr, s);
+    e = enqueue_batch(G, n_total, nnz, (const long long*)goff, rowptr, colidx, perm, base, L, s);
+    if (e == cudaSuccess) e = enqueue_latch((Ctl*)(base + L.ctl), stream_latch(s), nullptr, s);
     ws_free(ws, s);
     return e == cudaSuccess ? RCM_OK : cuda_status(e);
 }

@@ -1,0 +1,47 @@
+// rcm_batch.cuh -- the batched executor's arguments, its workspace layout and the enqueue step,
+// shared by rcm_order_batch and the serving path (which runs each request as a batch of one).
+#pragma once
+
+#include "rcm_internal.cuh"
+
+namespace rcm {
+
+struct BatchArgs {
+    int G;
+    const long long* goff;
+    // component tables: per-vertex arrays indexed by global id; per-graph lists at v0 (2 v0 for
+    // the sort scratch)
+    int* cc_parent;
+    int* cc_size;
+    unsigned long long* cc_key;
+    int* cc_roots;
+    unsigned long long* cc_gkey;
+    int* cc_gidx;
+    int4* cc_tab;
+    const int* rowptr;
+    const int4* ell;
+    const int* adj;
+    const int* deg;
+    unsigned long long* claim;
+    int* vis;
+    int* qa;
+    int* qb;
+    int* boff;
+    int* perm;
+    Ctl* ctl;
+};
+
+// Byte offsets of the workspace of N vertices (all graphs together) and nnz stored entries, each
+// 256-byte aligned; total = bytes to allocate.
+struct BatchLayout {
+    size_t ctl, pool, deg, claim, vis, big, adj, ell, ccs, cck, ccr, ccgk, ccgi, cct, total;
+};
+BatchLayout batch_layout(long long N, long long nnz);
+
+// Enqueues on s, with the workspace at base (laid out by batch_layout(n_total, nnz)):
+// control-block reset, structural checks (block structure when G > 1; rowptr[n_total] == nnz),
+// degrees, sorted rows, then the batched engine. Device-detected errors land in the control block.
+cudaError_t enqueue_batch(int G, long long n_total, int nnz, const long long* goff, const int* rowptr,
+                          const int* colidx, int* perm, char* base, const BatchLayout& L, cudaStream_t s);
+
+}  // namespace rcm

@@ -21,34 +21,40 @@ constexpr int kMaxComps = 1 << 20;   // components ordered concurrently at most 
 constexpr int kCompSmem = 8192;      // component tables sorted in shared memory up to this size
 
 // Representative of v; shortens the path on the way (benign races: a shortcut always points to
-// an ancestor, and parents only decrease).
-__device__ __forceinline__ int cc_root(volatile int* parent, int v) {
+// an ancestor, and parents only decrease). Every id on the path must lie in [lo, hi) and every
+// non-root must point to a smaller id; a path that breaks either rule (a parent entry that was
+// never initialised) returns -1 without following it.
+__device__ __forceinline__ int cc_root(volatile int* parent, int v, int lo, int hi) {
     int cur = parent[v];
-    if (cur != v) {
-        int prev = v, next;
-        while (cur > (next = parent[cur])) {
-            parent[prev] = next;
-            prev = cur;
-            cur = next;
-        }
+    if (cur == v) return v;
+    int prev = v;
+    while (true) {
+        if (cur < lo || cur >= hi) return -1;
+        const int next = parent[cur];
+        if (next >= cur) return next == cur ? cur : -1;
+        parent[prev] = next;
+        prev = cur;
+        cur = next;
     }
-    return cur;
 }
 
-__device__ __forceinline__ void cc_union(int* parent, int a, int b) {
+// Joins the sets of a and b. Returns false if a parent path was invalid (see cc_root).
+__device__ __forceinline__ bool cc_union(int* parent, int a, int b, int lo, int hi) {
     volatile int* vp = parent;
-    int ra = cc_root(vp, a), rb = cc_root(vp, b);
+    int ra = cc_root(vp, a, lo, hi), rb = cc_root(vp, b, lo, hi);
     while (ra != rb) {
+        if (ra < 0 || rb < 0) return false;
         if (ra < rb) {
             const int old = atomicCAS(&parent[rb], rb, ra);
-            if (old == rb) break;
-            rb = cc_root(vp, old);
+            if (old == rb) return true;
+            rb = cc_root(vp, old, lo, hi);
         } else {
             const int old = atomicCAS(&parent[ra], ra, rb);
-            if (old == ra) break;
-            ra = cc_root(vp, old);
+            if (old == ra) return true;
+            ra = cc_root(vp, old, lo, hi);
         }
     }
+    return ra >= 0;
 }
 
 }  // namespace rcm

@@ -67,6 +67,7 @@ struct EngineArgs {
     int* perm;                   // this graph's output segment (n ints); global ids while running
     Ctl* ctl;                    // grid control block (whole-grid executor only)
     int* status;                 // where device-detected error bits are ORed
+    int* diag;                   // optional (may be null): first failed guard's site and value
     int narrow_thr;
     int fused;
     int obits;                   // low bits of a key holding the in-level order
@@ -123,6 +124,8 @@ struct Engine {
     int sweep_id;
     int scan_par;          // alternates between consecutive CTA scans (see block_excl_scan)
     EngineSmem* sm;
+    unsigned long long* sm_sort = nullptr;  // component-table sort buffer (shared), if any
+    int sm_sort_cap = 0;
 
     // All threads call; args are copied to shared memory by thread 0.
     __device__ void init(const EngineArgs& args, EngineSmem* smem) {
@@ -165,6 +168,17 @@ struct Engine {
     }
     __device__ bool in_graph(int v) const { return (unsigned)(v - a->v0) < (unsigned)a->n; }
     __device__ void fail(int bits) { atomicOr(a->status, bits); }
+    // An index guard tripped: the run fails with kErrInternal; the first site and its offending
+    // value go to diag[0], diag[1] when a diagnostic word is given.
+    __device__ void fail_at(int site, int value) {
+        atomicOr(a->status, kErrInternal);
+        if (a->diag && atomicCAS(a->diag, 0, site) == 0) atomicExch(a->diag + 1, value);
+    }
+    // A component-table entry (start vertex, first label, size, root) that can be ordered with
+    // labels from at least nv.
+    __device__ bool tab_ok(const int4& t, int nv) const {
+        return in_graph(t.x) && t.y >= nv && t.z > 0 && (long long)t.y + t.z <= a->n;
+    }
     __device__ int cta_rank() const { return kCtaOnly ? 0 : (int)blockIdx.x; }
     __device__ int cta_count() const { return kCtaOnly ? 1 : (int)gridDim.x; }
 
@@ -422,7 +436,10 @@ struct Engine {
                         cb ^= 1;
                         F = cnt;
                         reached += cnt;
-                        ++ecc;
+                        if (++ecc > a->n) {
+                            fail_at(kSiteLevels, ecc);
+                            return false;
+                        }
                         if (!kCtaOnly && F >= a->narrow_thr) break;
                     }
                     if (kCtaOnly) {
@@ -736,7 +753,10 @@ struct Engine {
                         F = kids;
                         cur = nxt;
                         cb ^= 1;
-                        ++d;
+                        if (++d > a->n) {
+                            fail_at(kSiteLevels, d);
+                            return false;
+                        }
                         if (!kCtaOnly && F >= a->narrow_thr) break;
                     }
                     if (kCtaOnly) {
@@ -905,6 +925,10 @@ struct Engine {
     // all_left >= 0 (the number of vertices not yet numbered), the call stops after the first
     // sweep when the component is smaller than that, returning size = -1 (nothing numbered).
     __device__ bool component(int r, int nv, int& size, long long all_left = -1) {
+        if (!in_graph(r) || nv < 0 || nv >= a->n) {
+            fail_at(kSiteStart, r);
+            return false;
+        }
         int ecc_prev;
         unsigned long long k1;
         long long reached;
@@ -963,62 +987,72 @@ struct Engine {
         return true;
     }
 
-    // ---------------- concurrent components (whole-grid executor) ----------------
+    // ---------------- component table ----------------
     // Finds the components still unnumbered after labels [0, nv) and writes the component table
     // cc_tab (sorted by start key, label offsets from nv; see rcm_cc.cuh). Returns the number of
     // components, -1 when there are more than cc_cap (the caller continues one by one), -2 on a
-    // failed wait. sort_smem: kCompSmem keys + kCompSmem ints of dynamic shared memory.
-    __device__ int cc_prepare(int nv, unsigned long long* sort_smem) {
-        const int n = a->n;
-        Ctl* c = a->ctl;
-        const int stride = gridDim.x * blockDim.x;
-        const int first = blockIdx.x * blockDim.x + threadIdx.x;
-        for (int v = first; v < n; v += stride) {
+    // failed wait. sort_smem holds sort_cap keys + sort_cap ints of shared memory; larger tables
+    // sort in cc_gkey / cc_gidx.
+    __device__ int cc_prepare(int nv, unsigned long long* sort_smem, int sort_cap) {
+        const int n = a->n, v0 = a->v0;
+        int* counter = kCtaOnly ? &sm->bc[4] : &a->ctl->ncomp;
+        const int stride = cta_count() * blockDim.x;
+        const int first = cta_rank() * blockDim.x + threadIdx.x;
+        for (int i = first; i < n; i += stride) {
+            const int v = v0 + i;
             if (__ldcg(a->claim + v) == kClaimNone) {
                 a->cc_parent[v] = v;
                 a->cc_size[v] = 0;
                 a->cc_key[v] = kKeyMax;
             }
         }
-        if (blockIdx.x == 0 && threadIdx.x == 0) c->ncomp = 0;
+        if (cta_rank() == 0 && threadIdx.x == 0) *counter = 0;
         if (!barrier()) return -2;
-        for (int v = first; v < n; v += stride) {
+        for (int i = first; i < n; i += stride) {
+            const int v = v0 + i;
             if (__ldcg(a->claim + v) != kClaimNone) continue;
             int r[8];
             load_row(v, r);
             const int d = r[7];
 #pragma unroll
             for (int k = 0; k < kEllNb; ++k)
-                if (k < d && r[k] < v) cc_union(a->cc_parent, v, r[k]);
+                if (k < d && r[k] < v && !cc_union(a->cc_parent, v, r[k], v0, v0 + n)) fail_at(kSiteParent, v);
             if (d > kEllNb) {
                 const int rp = __ldg(a->rowptr + v);
                 for (int k = kEllNb; k < d; ++k) {
                     const int w = __ldg(a->adj + rp + k);
-                    if (w < v) cc_union(a->cc_parent, v, w);
+                    if (w < v && !cc_union(a->cc_parent, v, w, v0, v0 + n)) fail_at(kSiteParent, v);
                 }
             }
         }
         if (!barrier()) return -2;
-        for (int v = first; v < n; v += stride) {
+        for (int i = first; i < n; i += stride) {
+            const int v = v0 + i;
             if (__ldcg(a->claim + v) != kClaimNone) continue;
-            const int r = cc_root((volatile int*)a->cc_parent, v);
+            const int r = cc_root((volatile int*)a->cc_parent, v, v0, v0 + n);
+            if (r < 0) fail_at(kSiteParent, v);
             if (r == v) {
-                const int i = atomicAdd(&c->ncomp, 1);
-                if (i < a->cc_cap) a->cc_roots[i] = v;
+                const int k = atomicAdd(counter, 1);
+                if (k < a->cc_cap) a->cc_roots[k] = v;
             }
         }
         if (!barrier()) return -2;
-        if (threadIdx.x == 0) sm->bc[0] = ldcg(&c->ncomp);
+        if (threadIdx.x == 0) sm->bc[0] = kCtaOnly ? *counter : ldcg(counter);
         __syncthreads();
         const int C = sm->bc[0];
         __syncthreads();
         if (C > a->cc_cap) return -1;
         // sizes and start keys per root (lanes with the same root combine first)
         const int lane = threadIdx.x & 31;
-        for (int v0 = blockIdx.x * blockDim.x; v0 < n; v0 += stride) {
-            const int v = v0 + (int)threadIdx.x;
-            const bool ok = v < n && __ldcg(a->claim + v) == kClaimNone;
-            const int root = ok ? cc_root((volatile int*)a->cc_parent, v) : -1;
+        for (int i0 = cta_rank() * blockDim.x; i0 < n; i0 += stride) {
+            const int i = i0 + (int)threadIdx.x;
+            const int v = v0 + i;
+            bool ok = i < n && __ldcg(a->claim + v) == kClaimNone;
+            const int root = ok ? cc_root((volatile int*)a->cc_parent, v, v0, v0 + n) : -1;
+            if (ok && root < 0) {
+                fail_at(kSiteParent, v);
+                ok = false;
+            }
             unsigned long long key = ok ? pack_key(__ldg(a->deg + v), v) : kKeyMax;
             const unsigned grp = __match_any_sync(0xffffffffu, root);
             unsigned m = grp;
@@ -1034,12 +1068,12 @@ struct Engine {
             }
         }
         if (!barrier()) return -2;
-        // CTA 0: sort by key, label offsets from nv
-        if (blockIdx.x == 0) {
+        // one CTA: sort by key, label offsets from nv
+        if (cta_rank() == 0) {
             int P = 1;
             while (P < C) P <<= 1;
-            unsigned long long* sk = P <= kCompSmem ? sort_smem : a->cc_gkey;
-            int* si = P <= kCompSmem ? (int*)(sort_smem + kCompSmem) : a->cc_gidx;
+            unsigned long long* sk = P <= sort_cap ? sort_smem : a->cc_gkey;
+            int* si = P <= sort_cap ? (int*)(sort_smem + sort_cap) : a->cc_gidx;
             for (int i = threadIdx.x; i < P; i += blockDim.x) {
                 sk[i] = i < C ? __ldcg(a->cc_key + a->cc_roots[i]) : kKeyMax;
                 si[i] = i < C ? i : 0;
@@ -1067,16 +1101,18 @@ struct Engine {
             int carry = nv;
             for (int i0 = 0; i0 < C; i0 += blockDim.x) {
                 const int i = i0 + (int)threadIdx.x;
-                const int root = i < C ? a->cc_roots[si[i]] : 0;
+                const int root = i < C ? a->cc_roots[si[i]] : v0;
                 const int sz = i < C ? ldcg(a->cc_size + root) : 0;
                 int tot;
                 const int ex = cta_scan(sz, &tot);
                 if (i < C) a->cc_tab[i] = make_int4((int)(unsigned)(sk[i] & 0xffffffffu), carry + ex, sz, root);
                 carry += tot;
             }
-            if (threadIdx.x == 0 && carry != n) fail(kErrInternal);
+            if (threadIdx.x == 0 && carry != n) fail_at(kSiteTotal, carry);
         }
         if (!barrier()) return -2;
+        // a failed guard above leaves the table unusable (CTA runs have no exchange to report it)
+        if (kCtaOnly && (ld_volatile(a->status) & kErrInternal)) return -2;
         return C;
     }
 
@@ -1089,7 +1125,30 @@ struct Engine {
         stat_add(kStIsolated, Z);
         stat_add(kStComponents, Z);
         int nv = Z;
+        bool first = true, tried = false;
         while (nv < n) {
+            if (!first && !tried && a->cc_cap > 0) {
+                // more than one component: start keys and label ranges of all of them at once
+                tried = true;
+                const int C = cc_prepare(nv, sm_sort, sm_sort_cap);
+                if (C == -2) return false;
+                if (C > 0) {
+                    for (int i = 0; i < C; ++i) {
+                        const int4 t = a->cc_tab[i];
+                        if (!tab_ok(t, nv)) {
+                            fail_at(kSiteTable, i);
+                            return false;
+                        }
+                        int size;
+                        if (!component(t.x, t.y, size)) return false;
+                        if (size != t.z) {
+                            fail_at(kSiteSize, i);
+                            return false;
+                        }
+                    }
+                    return true;
+                }
+            }
             unsigned long long k0;
             tick(kPhOther);
             if (!next_start(k0)) return false;
@@ -1099,7 +1158,10 @@ struct Engine {
                 return false;
             }
             int size;
-            if (!component((int)(unsigned)(k0 & 0xffffffffu), nv, size)) return false;
+            const long long left = (first && a->cc_cap > 0) ? (long long)(n - nv) : -1;
+            first = false;
+            if (!component((int)(unsigned)(k0 & 0xffffffffu), nv, size, left)) return false;
+            if (size < 0) continue;
             nv += size;
         }
         return true;

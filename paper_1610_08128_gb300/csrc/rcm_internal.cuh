@@ -23,6 +23,17 @@ enum : int {
     kErrTooLarge = 8,   // a size beyond a fixed capacity
 };
 
+// Sites of the index guards that report through a diagnostic word (diag[0]; diag[1] holds the
+// offending value).
+enum : int {
+    kSiteStart = 1,   // a component start vertex or first label out of range
+    kSiteTable = 2,   // a component-table entry out of range (value: its index)
+    kSiteParent = 3,  // a union-find parent path left the graph (value: the vertex)
+    kSiteTotal = 4,   // component sizes do not add up to the vertices left (value: the sum)
+    kSiteSize = 5,    // a component's ordering reached a different size than its table entry
+    kSiteLevels = 6,  // a sweep ran more levels than the graph has vertices (value: the level)
+};
+
 // One CTA's slot of the grid exchange: flag = (epoch << 32) | count, written last with release.
 struct alignas(32) ExSlot {
     unsigned long long flag;

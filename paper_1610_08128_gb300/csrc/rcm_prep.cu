@@ -13,14 +13,14 @@
 
 namespace rcm {
 
-__global__ void k_degree_validate(int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
+__global__ void k_degree_validate(int n, int nnz, const int* __restrict__ rowptr, const int* __restrict__ colidx,
                                   int* __restrict__ deg, unsigned long long* __restrict__ claim, int* __restrict__ vis,
                                   int* __restrict__ bigrows, Ctl* ctl, int small_max) {
     __shared__ int s_max;
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
-    const int nnz = rowptr[n];
-    if (blockIdx.x == 0 && threadIdx.x == 0 && (rowptr[0] != 0 || nnz < 0)) atomicOr(&ctl->status, kErrBadCsr);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (rowptr[0] != 0 || rowptr[n] != nnz || nnz < 0))
+        atomicOr(&ctl->status, kErrBadCsr);
     int local_max = 0;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         const int a = rowptr[v], b = rowptr[v + 1];

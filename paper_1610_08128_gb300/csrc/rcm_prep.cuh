@@ -110,7 +110,9 @@ __device__ __forceinline__ void sort_big_row_cta(int v, const int* __restrict__ 
     __syncthreads();
 }
 
-__global__ void k_degree_validate(int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
+// nnz: the stored-entry count the caller sized its buffers for; rowptr[n] must equal it, and no
+// row is read beyond it.
+__global__ void k_degree_validate(int n, int nnz, const int* __restrict__ rowptr, const int* __restrict__ colidx,
                                   int* __restrict__ deg, unsigned long long* __restrict__ claim, int* __restrict__ vis,
                                   int* __restrict__ bigrows, Ctl* ctl, int small_max);
 

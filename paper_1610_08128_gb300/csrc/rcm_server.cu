@@ -7,15 +7,20 @@
 //    caller's buffer is in host memory), a status word and the workspace of the ordering.
 //    Requests are admitted in arrival order whenever a region and an in-flight slot are free; a
 //    request larger than the whole budget is refused at submission (RCM_ERR_TOO_LARGE).
-//  * Execution: each admitted request gets its own stream and one kernel launch of a single CTA
-//    that validates and preprocesses the pattern and runs the whole ordering (Engine<true>), so
-//    requests that arrive while others are on the GPU start as soon as they are admitted and run
-//    side by side on different SMs.
+//  * Execution: each admitted request gets its own stream and runs as a batch of one graph: the
+//    validation and sorted-row kernels, then the batched executor with one CTA (Engine<true>,
+//    rcm_batch.cu). Requests that arrive while others are on the GPU start as soon as they are
+//    admitted and run side by side on different SMs.
 //  * Completion: a host function enqueued after the result copy marks the request done, records
 //    its completion time and frees its region and slot; a worker thread admits waiting requests.
+//  * Failure: after a kernel fault the context is unusable and host functions behind the fault
+//    never run. While requests run, the worker polls their streams; a stream error finishes every
+//    running and waiting request with that error (and later submissions fail), so waiters return.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -24,94 +29,14 @@
 #include <unordered_map>
 #include <vector>
 
-#include "rcm_engine.cuh"
+#include "rcm_batch.cuh"
 #include "rcm_host.hpp"
 #include "rcm_internal.cuh"
-#include "rcm_prep.cuh"
 
 namespace rcm {
 
-constexpr int kReqThreads = 256;
-
-// Device buffers of one request (all inside its arena region, or the caller's device memory).
-struct ReqDesc {
-    int n;
-    int nnz;
-    const int* rowptr;
-    const int* colidx;
-    int* perm;
-    int* deg;
-    unsigned long long* claim;
-    int* vis;
-    int* pool4;   // queues / offsets; scratch of the long-row sorter during preprocessing
-    int* bigrows;
-    int* adj;
-    int4* ell;
-    int* status;
-};
-
-// One CTA orders one request: validation + degrees, sorted rows, then the engine.
-__global__ void __launch_bounds__(kReqThreads, 2) k_rcm_request(ReqDesc r) {
-    extern __shared__ unsigned long long s_keys[];  // kBigRowSmem keys for long rows
-    __shared__ EngineSmem smem;
-    __shared__ int s_nbig, s_m;
-    const int n = r.n;
-    if (threadIdx.x == 0) s_nbig = 0;
-    __syncthreads();
-    const int nnz = r.rowptr[n];
-    if (threadIdx.x == 0 && (r.rowptr[0] != 0 || nnz != r.nnz)) atomicOr(r.status, kErrBadCsr);
-    for (int v = threadIdx.x; v < n; v += blockDim.x) {
-        int d = 0;
-        if (!row_degree(n, nnz, r.rowptr, r.colidx, v, d)) atomicOr(r.status, kErrBadCsr);
-        else if (r.rowptr[v + 1] - r.rowptr[v] > kSmallRowMax) r.bigrows[atomicAdd(&s_nbig, 1)] = v;
-        r.deg[v] = d;
-        r.claim[v] = kClaimNone;
-        r.vis[v] = 0;
-    }
-    __syncthreads();
-    if (ld_volatile(r.status) & kErrBadCsr) return;
-    for (int v = threadIdx.x; v < n; v += blockDim.x)
-        if (r.rowptr[v + 1] - r.rowptr[v] <= kSmallRowMax) sort_small_row(v, r.rowptr, r.colidx, r.deg, r.adj, r.ell);
-    const int nbig = s_nbig;
-    for (int i = 0; i < nbig; ++i) {
-        const int v = r.bigrows[i];
-        int P = 1;
-        while (P < r.deg[v]) P <<= 1;
-        sort_big_row_cta(v, r.rowptr, r.colidx, r.deg, r.adj, r.ell,
-                         P <= kBigRowSmem ? s_keys : (unsigned long long*)r.pool4, &s_m);
-    }
-    __syncthreads();
-    EngineArgs a;
-    a.n = n;
-    a.v0 = 0;
-    a.rowptr = r.rowptr;
-    a.ell = r.ell;
-    a.adj = r.adj;
-    a.deg = r.deg;
-    a.claim = r.claim;
-    a.vis = r.vis;
-    a.qa = r.pool4;
-    a.qb = r.pool4 + n;
-    a.boff = r.pool4 + 2 * (size_t)n;
-    a.perm = r.perm;
-    a.ctl = nullptr;
-    a.status = r.status;
-    a.narrow_thr = 0x7fffffff;
-    a.fused = 1;
-    a.obits = claim_order_bits(n);
-    a.profile = 0;
-    a.limit_ns = 0;
-    a.cc_parent = a.cc_size = a.cc_roots = a.cc_gidx = nullptr;
-    a.cc_key = a.cc_gkey = nullptr;
-    a.cc_tab = nullptr;
-    a.cc_cap = 0;
-    a.cc_big = 0;
-    Engine<true> e;
-    e.init(a, &smem);
-    e.run();
-}
-
-// Bytes of the request region: inputs/outputs that must be staged, status word, workspace.
+// Arena bytes of one request: the staged CSR and result when they are in host memory, a 256-byte
+// header holding the graph offsets {0, n} of the batch of one, and the batched executor's workspace.
 static size_t request_bytes(long long n, long long nnz, bool stage_in, bool stage_out) {
     const size_t N = (size_t)std::max(n, 1LL), E = (size_t)std::max(nnz, 1LL);
     size_t o = 0;
@@ -121,15 +46,8 @@ static size_t request_bytes(long long n, long long nnz, bool stage_in, bool stag
         take(sizeof(int) * E);
     }
     if (stage_out) take(sizeof(int) * N);
-    take(256);                                  // status word
-    take(sizeof(int) * N);                      // deg
-    take(sizeof(unsigned long long) * N);       // claim
-    take(sizeof(int) * N);                      // vis
-    take(sizeof(int) * 4 * N);                  // pool4
-    take(sizeof(int) * N);                      // bigrows
-    take(sizeof(int) * E);                      // adj
-    take(sizeof(int4) * 2 * N);                 // ell
-    return o;
+    take(256);  // graph offsets
+    return o + batch_layout(std::max(n, 1LL), std::max(nnz, 0LL)).total;
 }
 
 // First-fit allocator over [0, size) with coalescing (host-side bookkeeping of the arena).
@@ -196,6 +114,7 @@ struct Request {
     size_t off = 0, bytes = 0;
     int slot = -1;
     int state = 0;  // 0 waiting, 1 running, 2 done
+    bool orphan = false;  // finished by the failure path: its host function may still be pending
     rcm_status status = RCM_OK;
     double t_submit = 0, t_start = 0, t_done = 0;
     Server* srv = nullptr;
@@ -208,7 +127,8 @@ struct Server {
     ArenaAlloc alloc;
     int max_inflight = 0;
     std::vector<cudaStream_t> streams;
-    int* h_status = nullptr;  // pinned, one word per slot
+    struct SlotHost* h_slots = nullptr;  // pinned, one per slot
+    std::vector<Request*> slot_req;  // running request of each slot
     std::vector<int> free_slots;
     std::mutex mu;
     std::condition_variable cv;
@@ -220,15 +140,27 @@ struct Server {
     uint64_t next_ticket = 1;
     long long submitted = 0, completed = 0, failed = 0, cancelled = 0;
     int running = 0, max_running = 0;
-    cudaError_t worker_error = cudaSuccess;
+    cudaError_t broken = cudaSuccess;  // first stream error seen: the context is unusable
+    bool trace = false;                // RCM_TRACE_ERRORS set: failed requests are reported on stderr
+};
+
+// Pinned host words of one slot: the graph offsets copied in, the status word copied out.
+struct alignas(64) SlotHost {
+    long long goff[2];
+    int status;
 };
 
 static void CUDART_CB on_request_done(void* p) {
     Request* r = (Request*)p;
     Server* s = r->srv;
     std::lock_guard<std::mutex> g(s->mu);
-    const int bits = *(volatile int*)&s->h_status[r->slot];
+    if (r->state == 2) return;  // already finished by the failure path
+    const int bits = *(const volatile int*)&s->h_slots[r->slot].status;
     r->status = r->status != RCM_OK ? r->status : status_from_bits(bits);
+    if (s->trace && r->status != RCM_OK)
+        std::fprintf(stderr, "rcm server: request %llu (n=%d, nnz=%lld) failed with device status bits %d\n",
+                     (unsigned long long)r->ticket, r->n, r->nnz, bits);
+    s->slot_req[r->slot] = nullptr;
     r->t_done = now_s();
     r->state = 2;
     s->alloc.release(r->off, r->bytes);
@@ -265,31 +197,70 @@ static rcm_status launch_request(Server* s, Request* r) {
         colidx = d_ci;
     }
     if (r->out_host) perm = (int*)take(sizeof(int) * N);
-    ReqDesc d;
-    d.n = r->n;
-    d.nnz = (int)r->nnz;
-    d.rowptr = rowptr;
-    d.colidx = colidx;
-    d.perm = perm;
-    d.status = (int*)take(256);
-    d.deg = (int*)take(sizeof(int) * N);
-    d.claim = (unsigned long long*)take(sizeof(unsigned long long) * N);
-    d.vis = (int*)take(sizeof(int) * N);
-    d.pool4 = (int*)take(sizeof(int) * 4 * N);
-    d.bigrows = (int*)take(sizeof(int) * N);
-    d.adj = (int*)take(sizeof(int) * E);
-    d.ell = (int4*)take(sizeof(int4) * 2 * N);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d.status, 0, sizeof(int), st);
-    if (e == cudaSuccess) {
-        k_rcm_request<<<1, kReqThreads, sizeof(unsigned long long) * kBigRowSmem, st>>>(d);
-        e = cudaGetLastError();
-    }
+    long long* d_goff = (long long*)take(256);
+    const BatchLayout L = batch_layout(std::max(r->n, 1), std::max(r->nnz, 0LL));
+    char* ws = take(L.total);
+    SlotHost* hs = &s->h_slots[r->slot];
+    hs->goff[0] = 0;
+    hs->goff[1] = r->n;
+    hs->status = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_goff, hs->goff, sizeof(hs->goff), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = enqueue_batch(1, r->n, (int)r->nnz, d_goff, rowptr, colidx, perm, ws, L, st);
     if (e == cudaSuccess && r->out_host)
         e = cudaMemcpyAsync(r->perm, perm, sizeof(int) * (size_t)r->n, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&s->h_status[r->slot], d.status, sizeof(int), cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(&hs->status, ws + L.ctl + offsetof(Ctl, status), sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaLaunchHostFunc(st, on_request_done, r);
     return e == cudaSuccess ? RCM_OK : cuda_status(e);
+}
+
+// Finishes every running and waiting request with the stream error e (caller holds the lock).
+// Running requests stay allocated: a host function of theirs that is already waiting for the
+// lock returns without touching anything else once it sees them done.
+static void fail_all(Server* s, cudaError_t e) {
+    s->broken = e;
+    const rcm_status st = cuda_status(e);
+    const double t = now_s();
+    for (int i = 0; i < s->max_inflight; ++i) {
+        Request* r = s->slot_req[i];
+        if (!r) continue;
+        s->slot_req[i] = nullptr;
+        r->status = st;
+        r->state = 2;
+        r->orphan = true;
+        r->t_done = t;
+        s->running--;
+        s->completed++;
+        s->failed++;
+    }
+    for (Request* r : s->waiting) {
+        r->status = st;
+        r->state = 2;
+        r->t_done = t;
+        s->completed++;
+        s->failed++;
+    }
+    s->waiting.clear();
+    s->cv.notify_all();
+}
+
+// Polls the streams of running requests; a stream error means a fault on the device (caller
+// holds the lock, which is released around the queries).
+static void check_streams(Server* s, std::unique_lock<std::mutex>& lk) {
+    std::vector<int> slots;
+    for (int i = 0; i < s->max_inflight; ++i)
+        if (s->slot_req[i]) slots.push_back(i);
+    lk.unlock();
+    cudaError_t bad = cudaSuccess;
+    for (int i : slots) {
+        const cudaError_t e = cudaStreamQuery(s->streams[i]);
+        if (e != cudaSuccess && e != cudaErrorNotReady) {
+            bad = e;
+            break;
+        }
+    }
+    lk.lock();
+    if (bad != cudaSuccess && s->broken == cudaSuccess) fail_all(s, bad);
 }
 
 static void worker_loop(Server* s) {
@@ -306,6 +277,7 @@ static void worker_loop(Server* s) {
             r->off = off;
             r->slot = s->free_slots.back();
             s->free_slots.pop_back();
+            s->slot_req[r->slot] = r;
             r->state = 1;
             r->t_start = now_s();
             s->running++;
@@ -321,6 +293,8 @@ static void worker_loop(Server* s) {
                     // stream, then release it as failed
                     cudaStreamSynchronize(s->streams[r->slot]);
                     std::lock_guard<std::mutex> g(s->mu);
+                    if (r->state == 2) continue;  // finished by the failure path meanwhile
+                    s->slot_req[r->slot] = nullptr;
                     r->status = st;
                     r->state = 2;
                     r->t_done = now_s();
@@ -336,7 +310,12 @@ static void worker_loop(Server* s) {
             continue;
         }
         if (s->stop && s->waiting.empty() && s->running == 0) break;
-        s->cv.wait(lk);
+        if (s->running > 0 && s->broken == cudaSuccess) {
+            s->cv.wait_for(lk, std::chrono::milliseconds(20));
+            check_streams(s, lk);
+        } else {
+            s->cv.wait(lk);
+        }
     }
 }
 
@@ -349,6 +328,11 @@ struct rcm_server {
 };
 
 extern "C" {
+
+size_t rcm_request_bytes(int32_t n, int64_t nnz, int32_t host_csr, int32_t host_out) {
+    if (n < 0 || nnz < 0) return 0;
+    return request_bytes(n, nnz, host_csr != 0, host_out != 0);
+}
 
 rcm_status rcm_server_create(size_t hbm_budget_bytes, int32_t max_inflight, rcm_server** out) {
     if (!out || hbm_budget_bytes == 0 || max_inflight <= 0 || max_inflight > 4096) return RCM_ERR_INVALID_ARG;
@@ -364,16 +348,16 @@ rcm_status rcm_server_create(size_t hbm_budget_bytes, int32_t max_inflight, rcm_
         delete srv;
         return cuda_status(e);
     }
-    e = cudaHostAlloc((void**)&s.h_status, sizeof(int) * (size_t)max_inflight, cudaHostAllocDefault);
+    e = cudaHostAlloc((void**)&s.h_slots, sizeof(SlotHost) * (size_t)max_inflight, cudaHostAllocDefault);
     if (e != cudaSuccess) {
         cudaFree(s.arena);
         delete srv;
         return cuda_status(e);
     }
-    e = cudaFuncSetAttribute(k_rcm_request, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(unsigned long long) * kBigRowSmem));
     s.alloc.reset(s.budget);
     s.max_inflight = max_inflight;
+    s.slot_req.assign(max_inflight, nullptr);
+    s.trace = std::getenv("RCM_TRACE_ERRORS") != nullptr;
     s.streams.resize(max_inflight);
     for (int i = 0; i < max_inflight && e == cudaSuccess; ++i) {
         e = cudaStreamCreateWithFlags(&s.streams[i], cudaStreamNonBlocking);
@@ -382,7 +366,7 @@ rcm_status rcm_server_create(size_t hbm_budget_bytes, int32_t max_inflight, rcm_
     if (e != cudaSuccess) {
         for (cudaStream_t st : s.streams)
             if (st) cudaStreamDestroy(st);
-        cudaFreeHost(s.h_status);
+        cudaFreeHost(s.h_slots);
         cudaFree(s.arena);
         delete srv;
         return cuda_status(e);
@@ -422,6 +406,10 @@ rcm_status rcm_submit(rcm_server* srv, int32_t n, int64_t nnz, const int32_t* ro
         delete r;
         return RCM_ERR_INVALID_ARG;
     }
+    if (s.broken != cudaSuccess) {
+        delete r;
+        return cuda_status(s.broken);
+    }
     if (r->bytes > s.budget) {
         delete r;
         return RCM_ERR_TOO_LARGE;
@@ -446,7 +434,7 @@ static rcm_status finish(Server& s, std::unordered_map<uint64_t, Request*>::iter
     Request* r = it->second;
     const rcm_status st = r->status;
     s.reqs.erase(it);
-    delete r;
+    if (!r->orphan) delete r;  // an orphan's host function may still hold it (see fail_all)
     return st;
 }
 
@@ -532,9 +520,10 @@ rcm_status rcm_server_destroy(rcm_server* srv) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
     }
-    for (auto& kv : s.reqs) delete kv.second;
+    for (auto& kv : s.reqs)
+        if (!kv.second->orphan) delete kv.second;
     s.reqs.clear();
-    cudaFreeHost(s.h_status);
+    cudaFreeHost(s.h_slots);
     cudaFree(s.arena);
     delete srv;
     return RCM_OK;

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rcm_single(EngineArgs args, int
         if (!first && !tried && args.cc_cap > 0) {
             // more than one component: order them concurrently (one attempt)
             tried = true;
-            C = e.cc_prepare(nv, s_sort);
+            C = e.cc_prepare(nv, s_sort, kCompSmem);
             if (C == -2) return;
             if (C > 0) break;
         }
@@ -55,6 +55,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_rcm_single(EngineArgs args, int
         // large components on the whole grid, one after another
         for (int i = 0; i < C; ++i) {
             const int4 t = __ldcg(args.cc_tab + i);
+            if (!e.tab_ok(t, nv)) {
+                e.fail_at(kSiteTable, i);
+                return;
+            }
             if (t.z < args.cc_big) continue;
             int size;
             if (!e.component(t.x, t.y, size)) return;
@@ -84,6 +88,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_rcm_single(EngineArgs args, int
         __syncthreads();
         if (i >= C) break;
         const int4 t = __ldcg(args.cc_tab + i);
+        if (!e.tab_ok(t, nv)) {
+            e.fail_at(kSiteTable, i);
+            return;
+        }
         if (t.z >= args.cc_big) continue;
         EngineArgs ca = args;
         ca.qa = args.qa + t.y;
@@ -118,11 +126,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_rcm_single(EngineArgs args, int
     }
 }
 
-// The stored-entry count the host sized the workspace for must match rowptr[n] (otherwise the
-// sorted-adjacency copy would not fit).
-__global__ void k_init_ctl(Ctl* ctl, int nnz, const int* rowptr_n) {
-    if (threadIdx.x == 0 && *rowptr_n != nnz) ctl->status |= kErrBadCsr;
-}
 
 // ------------------------------------------------------------------------------------------
 // host side
@@ -203,6 +206,7 @@ constexpr int kSingleDynSmem = (int)((sizeof(unsigned long long) + sizeof(int)) 
 static int single_blocks_per_sm(int threads) {
     std::lock_guard<std::mutex> g(g_single_mu);
     const int idx = threads_index(threads);
+    if (idx < 0) return 0;  // not a supported block size (the options check rejects it first)
     if (g_single_blocks_per_sm[idx] < 0) {
         int b = 0;
         cudaFuncSetAttribute(single_kernel(threads), cudaFuncAttributeMaxDynamicSharedMemorySize, kSingleDynSmem);
@@ -255,13 +259,14 @@ rcm_status order_single(int32_t n, int64_t nnz, const int32_t* rowptr, const int
     if (ev) e = cudaEventRecord(ev[0], s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), s);
     if (e == cudaSuccess) {
-        k_init_ctl<<<1, 32, 0, s>>>(ctl, (int)nnz, rowptr + n);
         const int pb = 256;
         const int pgrid = (int)std::min<long long>((n + pb - 1) / pb, (long long)di.sms * 16);
-        k_degree_validate<<<std::max(pgrid, 1), pb, 0, s>>>(n, rowptr, colidx, deg, claim, vis, bigrows, ctl,
+        k_degree_validate<<<std::max(pgrid, 1), pb, 0, s>>>(n, (int)nnz, rowptr, colidx, deg, claim, vis, bigrows, ctl,
                                                            kSmallRowMax);
         k_sort_rows_small<<<std::max(pgrid, 1), pb, 0, s>>>(n, rowptr, colidx, deg, adj, ell, ctl);
-        k_sort_rows_big<<<di.sms * 2, 1024, sizeof(unsigned long long) * kBigRowSmem, s>>>(
+        // rows longer than kSmallRowMax entries number at most nnz / (kSmallRowMax + 1)
+        const int big_grid = (int)std::max<long long>(1, std::min<long long>(2LL * di.sms, nnz / (kSmallRowMax + 1)));
+        k_sort_rows_big<<<big_grid, 1024, sizeof(unsigned long long) * kBigRowSmem, s>>>(
             n, rowptr, colidx, deg, adj, ell, bigrows, ctl, (unsigned long long*)pool4);
         e = cudaGetLastError();
         if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
@@ -282,6 +287,7 @@ rcm_status order_single(int32_t n, int64_t nnz, const int32_t* rowptr, const int
         args.perm = perm;
         args.ctl = ctl;
         args.status = &ctl->status;
+        args.diag = nullptr;
         args.narrow_thr = narrow;
         args.obits = obits;
         args.profile = o.profile_phases ? 1 : 0;
@@ -397,13 +403,14 @@ rcm_status order_single_noalloc(int32_t n, const int32_t* rowptr, const int32_t*
     // other per-vertex array is initialised by the kernels below
     e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), s);
     if (e == cudaSuccess) {
-        k_init_ctl<<<1, 32, 0, s>>>(ctl, nnz, rowptr + n);
         const int pb = 256;
         const int pgrid = (int)std::min<long long>((n + pb - 1) / pb, (long long)di.sms * 16);
-        k_degree_validate<<<std::max(pgrid, 1), pb, 0, s>>>(n, rowptr, colidx, deg, claim, vis, bigrows, ctl,
+        k_degree_validate<<<std::max(pgrid, 1), pb, 0, s>>>(n, (int)nnz, rowptr, colidx, deg, claim, vis, bigrows, ctl,
                                                            kSmallRowMax);
         k_sort_rows_small<<<std::max(pgrid, 1), pb, 0, s>>>(n, rowptr, colidx, deg, adj, ell, ctl);
-        k_sort_rows_big<<<di.sms * 2, 1024, sizeof(unsigned long long) * kBigRowSmem, s>>>(
+        // rows longer than kSmallRowMax entries number at most nnz / (kSmallRowMax + 1)
+        const int big_grid = (int)std::max<long long>(1, std::min<long long>(2LL * di.sms, nnz / (kSmallRowMax + 1)));
+        k_sort_rows_big<<<big_grid, 1024, sizeof(unsigned long long) * kBigRowSmem, s>>>(
             n, rowptr, colidx, deg, adj, ell, bigrows, ctl, (unsigned long long*)pool4);
         e = cudaGetLastError();
     }
@@ -423,6 +430,7 @@ rcm_status order_single_noalloc(int32_t n, const int32_t* rowptr, const int32_t*
         args.perm = perm;
         args.ctl = ctl;
         args.status = &ctl->status;
+        args.diag = nullptr;
         args.narrow_thr = std::min(2 * threads, kCache);
         args.obits = obits;
         args.profile = 0;

@@ -90,6 +90,7 @@ def load():
         "rcm_stream_status": ([P], ctypes.c_int),
         "rcm_workspace_bytes": ([I32, I64], SZ),
         "rcm_bandwidth_profile": ([I32, P, P, P, ctypes.POINTER(I64), ctypes.POINTER(I64), P], ctypes.c_int),
+        "rcm_request_bytes": ([I32, I64, I32, I32], SZ),
         "rcm_server_create": ([SZ, I32, ctypes.POINTER(P)], ctypes.c_int),
         "rcm_submit": ([P, I32, I64, P, P, P, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
         "rcm_poll": ([P, ctypes.c_uint64], ctypes.c_int),
@@ -192,6 +193,10 @@ def rcm_bandwidth_profile(n, rowptr, colidx, perm, stream=None):
                                       _ptr(perm, True, _i32()), ctypes.byref(bw), ctypes.byref(prof),
                                       _stream(stream))
     return st, int(bw.value), int(prof.value)
+
+
+def rcm_request_bytes(n, nnz, host_csr=True, host_out=True) -> int:
+    return int(load().rcm_request_bytes(int(n), int(nnz), int(bool(host_csr)), int(bool(host_out))))
 
 
 def rcm_server_create(hbm_budget_bytes, max_inflight):

@@ -377,23 +377,52 @@ def mix_sizes(count: int, lo: float, hi: float, seed) -> tuple[np.ndarray, np.nd
     return sizes, kinds
 
 
-def c4_batch(G: int = 10_000, nmin: int = 100, nmax: int = 50_000, seed_offset: int = 0) -> Batch:
+def _make_graphs(specs):
+    return [batch_graph(k, s, seed) for k, s, seed in specs]
+
+
+def make_graphs(specs, workers: int = 0):
+    """batch_graph for every (kind, n, seed) spec; with workers > 1 the specs are split over a
+    process pool started with 'spawn' (safe in processes that already use the GPU)."""
+    specs = list(specs)
+    if workers <= 1 or len(specs) < 64:
+        return _make_graphs(specs)
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    chunks = [specs[i::workers] for i in range(workers)]
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        parts = list(ex.map(_make_graphs, chunks))
+    out = [None] * len(specs)
+    for w, part in enumerate(parts):
+        out[w::workers] = part
+    return out
+
+
+def default_workers() -> int:
+    import os
+
+    return max(1, min(32, len(os.sched_getaffinity(0))))
+
+
+def c4_batch(G: int = 10_000, nmin: int = 100, nmax: int = 50_000, seed_offset: int = 0, workers: int = 1) -> Batch:
     """G independent graphs, vertex counts log-uniform in [nmin, nmax], kind uniform over
     {2D grid, 3D grid, kNN(3) mesh}, ids permuted per graph, concatenated block-diagonally."""
     base = SEED_BASE + 4 + 1000 * seed_offset
     sizes, kinds = mix_sizes(G, nmin, nmax, base)
-    graphs = [batch_graph(int(k), int(s), [base, i]) for i, (k, s) in enumerate(zip(kinds, sizes))]
-    return concat(graphs)
+    specs = [(int(k), int(s), [base, i]) for i, (k, s) in enumerate(zip(kinds, sizes))]
+    return concat(make_graphs(specs, workers))
 
 
 def c5_trace(requests: int = 4000, rate_per_s: float = 2000.0, pool: int = 256,
-             nmin: float = 1e3, nmax: float = 4e6, seed_offset: int = 0):
+             nmin: float = 1e3, nmax: float = 4e6, seed_offset: int = 0, workers: int = 1):
     """Serving workload: Poisson arrival times (mean gap 1/rate) over ``requests`` requests, each
     naming one graph of a pool of ``pool`` pre-generated graphs with log-uniform sizes in
     [nmin, nmax] from the three batch generators. Returns (arrival_s, pool_index, pool graphs)."""
     base = SEED_BASE + 5 + 1000 * seed_offset
     sizes, kinds = mix_sizes(pool, nmin, nmax, [base, 1])
-    graphs = [batch_graph(int(k), int(s), [base, 2, i]) for i, (k, s) in enumerate(zip(kinds, sizes))]
+    specs = [(int(k), int(s), [base, 2, i]) for i, (k, s) in enumerate(zip(kinds, sizes))]
+    graphs = make_graphs(specs, workers)
     rng = rng_for([base, 3])
     gaps = rng.exponential(1.0 / rate_per_s, requests)
     arrival = np.cumsum(gaps) - gaps[0]

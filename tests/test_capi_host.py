@@ -48,6 +48,12 @@ def test_host_only_functions(lib):
     ws = rcm.rcm_workspace_bytes(4096, 16128)
     assert ws >= 4 * (8 * 4096 + 16128)
     assert rcm.rcm_workspace_bytes(-1, 0) == 0
+    # a server request holds the workspace plus what it stages
+    both = rcm.rcm_request_bytes(4096, 16128, True, True)
+    assert both > rcm.rcm_request_bytes(4096, 16128, False, False) + 4 * (2 * 4096 + 16128)
+    # staging the output adds its 4n bytes (4 * 4096 is already a multiple of the 256-byte alignment)
+    assert rcm.rcm_request_bytes(4096, 16128, False, True) == rcm.rcm_request_bytes(4096, 16128, False, False) + 4 * 4096
+    assert rcm.rcm_request_bytes(-1, 0) == 0
 
 
 def test_binding_refuses_missing_library(monkeypatch, tmp_path):

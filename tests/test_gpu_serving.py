@@ -23,9 +23,10 @@ def rcm():
 
 
 def region_bytes(g):
-    """Arena bytes of one request with host-resident buffers: staged CSR and output (8 bytes per
-    vertex plus 4 per entry), workspace (68 per vertex plus 4 per entry), alignment slack."""
-    return 76 * g.n + 8 * g.nnz + 64 * 1024
+    """Arena bytes of one request with host-resident buffers (staged CSR and output)."""
+    from paper_1610_08128_gb300 import rcm as r
+
+    return r.rcm_request_bytes(g.n, g.nnz, True, True)
 
 
 def mix(count, seed, lo=200, hi=60000):
