@@ -40,7 +40,7 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--side", type=int, default=SIDE)
-    p.add_argument("--cpu-samples", type=int, default=3)
+    p.add_argument("--cpu-samples", type=int, default=6)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true")
@@ -219,20 +219,17 @@ def bench_batched(args, torch, rcm, synth, workers):
     return {"workload": f"{b.G} graphs, n log-uniform 100..50,000, 2D grid / 3D grid / kNN(3) mesh",
             "vertices": b.n, "entries": int(b.rowptr[-1]), "ms": t * 1e3, "orderings_per_s": b.G / t,
             "plain_orderings_per_s": 1.0 / t_plain, "plain_sample": len(dev), "vs_plain": (b.G / t) * t_plain,
-            "sample_equal_to_plain": bool(same), "gpu_launches": 5}
+            "sample_equal_to_plain": bool(same),
+            # k_batch_validate, k_degree_validate, k_sort_rows_small, k_sort_rows_big, k_rcm_batch, k_latch
+            "gpu_launches": 6}
 
 
-def bench_served(args, torch, rcm, synth, workers):
-    """Poisson request stream replayed through the server (continuous batching), against the same
-    trace served FIFO by rcm_order_host (simulated from measured per-graph service times)."""
-    import numpy as np
-
+def served_setup(args, torch, rcm, synth, workers):
+    """The served trace (Poisson arrivals over a pool of graphs, pinned host buffers) and the same
+    trace served FIFO by rcm_order_host, simulated from per-graph service times measured here."""
     arrival, which, pool = synth.c5_trace(requests=args.serve_requests, rate_per_s=args.serve_rate,
                                           pool=args.serve_pool, workers=workers)
-    bufs = []
-    for g in pool:
-        bufs.append((torch.from_numpy(g.rowptr).pin_memory(), torch.from_numpy(g.colidx).pin_memory()))
-    # FIFO baseline service times through the plain host API
+    bufs = [(torch.from_numpy(g.rowptr).pin_memory(), torch.from_numpy(g.colidx).pin_memory()) for g in pool]
     service = []
     for g, (r, c) in zip(pool, bufs):
         out = torch.empty(g.n, dtype=torch.int32).pin_memory()
@@ -244,9 +241,16 @@ def bench_served(args, torch, rcm, synth, workers):
     for t_a, gi in zip(arrival, which):
         fin = max(fin, t_a) + service[gi]
         lat.append(fin - t_a)
-    fifo_rate = len(arrival) / fin
-    # served
-    st, srv = rcm.rcm_server_create(60 << 30, 256)
+    return {"arrival": arrival, "which": which, "pool": pool, "bufs": bufs, "fifo_rate": len(arrival) / fin,
+            "fifo_p50": pct(lat, 0.5), "fifo_p99": pct(lat, 0.99)}
+
+
+def served_run(args, torch, rcm, setup, options=None, check=True):
+    """Replays the trace through the server (continuous batching) in real time."""
+    import numpy as np
+
+    arrival, which, pool, bufs = setup["arrival"], setup["which"], setup["pool"], setup["bufs"]
+    st, srv = rcm.rcm_server_create_ex(60 << 30, 256, options)
     rcm.check(st, "rcm_server_create")
     outs = [torch.empty(pool[gi].n, dtype=torch.int32).pin_memory() for gi in which]
     tickets = []
@@ -263,22 +267,28 @@ def bench_served(args, torch, rcm, synth, workers):
     t_total = time.perf_counter() - t_start
     _, info = rcm.rcm_server_info(srv)
     rcm.rcm_server_destroy(srv)
-    # results served in the mix equal the plain path's
     same = True
-    for k in range(0, len(which), max(1, len(which) // 16)):
-        g = pool[which[k]]
-        ref = torch.empty(g.n, dtype=torch.int32).pin_memory()
-        rcm.check(rcm.rcm_order_host(g.n, bufs[which[k]][0], bufs[which[k]][1], ref), "plain")
-        same &= bool(torch.equal(ref, outs[k]))
+    if check:  # results served in the mix equal the plain path's
+        for k in range(0, len(which), max(1, len(which) // 16)):
+            g = pool[which[k]]
+            ref = torch.empty(g.n, dtype=torch.int32).pin_memory()
+            rcm.check(rcm.rcm_order_host(g.n, bufs[which[k]][0], bufs[which[k]][1], ref), "plain")
+            same &= bool(torch.equal(ref, outs[k]))
     sizes = [pool[gi].n for gi in which]
     return {"workload": f"{len(arrival)} requests, Poisson {args.serve_rate:.0f}/s, pool of {len(pool)} graphs "
                         f"(n log-uniform 1e3..4e6, 3 generators), 60 GB budget",
             "mean_vertices": float(np.mean(sizes)), "orderings_per_s": len(arrival) / t_total,
             "p50_ms": info["latency_p50_s"] * 1e3, "p99_ms": info["latency_p99_s"] * 1e3,
             "max_concurrent": info["max_running"], "arena_peak_gb": info["arena_peak_bytes"] / 1e9,
-            "fifo_plain_orderings_per_s": fifo_rate, "fifo_plain_p50_ms": pct(lat, 0.5) * 1e3,
-            "fifo_plain_p99_ms": pct(lat, 0.99) * 1e3, "vs_fifo_plain": (len(arrival) / t_total) / fifo_rate,
-            "served_equal_to_plain": same}
+            "fifo_plain_orderings_per_s": setup["fifo_rate"], "fifo_plain_p50_ms": setup["fifo_p50"] * 1e3,
+            "fifo_plain_p99_ms": setup["fifo_p99"] * 1e3,
+            "vs_fifo_plain": (len(arrival) / t_total) / setup["fifo_rate"], "served_equal_to_plain": same}
+
+
+def bench_served(args, torch, rcm, synth, workers):
+    """Poisson request stream replayed through the server, against the same trace served FIFO by
+    rcm_order_host."""
+    return served_run(args, torch, rcm, served_setup(args, torch, rcm, synth, workers))
 
 
 def run_reference(args):
@@ -444,7 +454,8 @@ def main():
             "config": dict(cfg, parallelism="replicas" if world > 1 else "single",
                            l2="inputs larger than L2, and a 2x-L2 buffer is written between steps"),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": 6 * args.steps, "clocks": clocks,
+            # per step: k_degree_validate, k_sort_rows_small, k_sort_rows_big, k_rcm_single, k_latch
+            "gpu_launches": 5 * args.steps, "clocks": clocks,
             "stats": dict(stats, prep_ms=statistics.mean(prep_ms), traverse_ms=trav),
             "quality": {"bandwidth": bw, "profile": prof},
             "batched": batched, "served": served,

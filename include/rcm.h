@@ -78,7 +78,16 @@ typedef struct {
                                     the others' bounded waits run out and report RCM_ERR_TIMEOUT  */
     int32_t profile_phases;    /* 1 = CTA 0 accumulates %globaltimer time per phase into
                                   rcm_stats.phase_ns (small overhead)                              */
-    int32_t reserved[2];
+    int32_t cluster;           /* 1 = launch the persistent engine as ONE thread-block cluster of
+                                  grid_blocks CTAs (2..16 as the device allows; 0 = the largest),
+                                  co-scheduled by the hardware, instead of a cooperative grid;
+                                  block_threads must be 0 or 512. RCM_ERR_INVALID_ARG if the
+                                  device cannot launch that cluster                                */
+    int32_t executor;          /* 0 = automatic: graphs of at most 4,608 vertices, with the grid options
+                                  above at their defaults, run on one CTA that keeps the graph's
+                                  traversal state in shared memory; others on the persistent grid.
+                                  1 = always the persistent grid. 2 = always the shared-memory CTA
+                                  (RCM_ERR_TOO_LARGE above 4,608 vertices)                          */
 } rcm_options;
 
 /* Statistics of one ordering (filled by rcm_order_ex when requested). */
@@ -201,6 +210,20 @@ size_t rcm_request_bytes(int32_t n, int64_t nnz, int32_t host_csr, int32_t host_
 
 /* Creates a server on the current device. max_inflight in [1, 4096]. */
 rcm_status rcm_server_create(size_t hbm_budget_bytes, int32_t max_inflight, rcm_server **out);
+
+/* Execution policy of a server (rcm_server_create uses the defaults, all fields 0). */
+typedef struct {
+    int64_t cluster_min_vertices; /* requests of at least this many vertices run the persistent
+                                     engine of rcm_order launched as one thread-block cluster;
+                                     smaller ones run on one CTA. 0 = 262,144; -1 = never         */
+    int32_t cluster_blocks;       /* CTAs of that cluster, 2..16 as the device allows; 0 = largest */
+    int32_t reserved[5];
+} rcm_server_options;
+
+/* rcm_server_create with an execution policy (opts may be NULL). RCM_ERR_INVALID_ARG for values
+   outside the ranges above. */
+rcm_status rcm_server_create_ex(size_t hbm_budget_bytes, int32_t max_inflight, const rcm_server_options *opts,
+                                rcm_server **out);
 
 /*
  * Submits one ordering request and returns its ticket. rowptr/colidx may be host or device

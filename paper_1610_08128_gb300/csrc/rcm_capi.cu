@@ -8,6 +8,7 @@
 #include "rcm_internal.cuh"
 #include "rcm_cc.cuh"
 #include "rcm_prep.cuh"
+#include "rcm_single.cuh"
 
 namespace rcm {
 
@@ -142,6 +143,8 @@ static rcm_status check_options(const rcm_options* o) {
         return RCM_ERR_INVALID_ARG;
     const int t = o->block_threads;
     if (t && t != 32 && t != 64 && t != 128 && t != 256 && t != 512 && t != 1024) return RCM_ERR_INVALID_ARG;
+    if (o->cluster != 0 && o->cluster != 1) return RCM_ERR_INVALID_ARG;
+    if (o->executor < 0 || o->executor > 2) return RCM_ERR_INVALID_ARG;
     return RCM_OK;
 }
 
@@ -168,18 +171,7 @@ const char* rcm_status_string(rcm_status s) {
 
 size_t rcm_workspace_bytes(int32_t n, int64_t nnz) {
     if (n < 0 || nnz < 0) return 0;
-    size_t o = 0;
-    auto take = [&](size_t bytes) { o = align_up(o + bytes, 256); };
-    const size_t N = (size_t)std::max(n, 1);
-    take(sizeof(Ctl));
-    take(sizeof(int) * 4 * N);
-    take(sizeof(int) * N);
-    take(sizeof(unsigned long long) * N);
-    take(sizeof(int) * N);
-    take(sizeof(int) * N);
-    take(sizeof(int) * (size_t)std::max<int64_t>(nnz, 1));
-    take(sizeof(int) * 8 * N);
-    return o;
+    return single_layout(n, nnz).total;
 }
 
 rcm_status rcm_order_ex(int32_t n, const int32_t* rowptr, const int32_t* colidx, int32_t* perm_out,

@@ -117,8 +117,12 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-template <bool kCtaOnly>
+// kSmem (CTA engines only): the claims, visit stamps and padded rows of the graph live in shared
+// memory, indexed from the graph's first vertex v0; otherwise they are global arrays indexed by
+// vertex id.
+template <bool kCtaOnly, bool kSmem = false>
 struct Engine {
+    static_assert(kCtaOnly || !kSmem, "shared-memory state needs a CTA engine");
     const EngineArgs* a;   // in shared memory (keeps the per-thread register footprint small)
     unsigned epoch;
     int sweep_id;
@@ -184,12 +188,29 @@ struct Engine {
 
     // Bring a vertex's padded row into L2 ahead of the level that will read it.
     __device__ void prefetch_row(int u) const {
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(a->ell + 2 * (size_t)u));
+        if constexpr (!kSmem) asm volatile("prefetch.global.L2 [%0];" ::"l"(a->ell + 2 * (size_t)u));
+    }
+
+    __device__ unsigned long long* claim_p(int v) const { return a->claim + (kSmem ? v - a->v0 : v); }
+    __device__ int* vis_p(int v) const { return a->vis + (kSmem ? v - a->v0 : v); }
+    // Claims are updated by atomics: global ones are read from L2 (other CTAs' atomics, and no
+    // stale L1 line); shared-memory ones with plain loads.
+    __device__ unsigned long long ld_claim(int v) const {
+        if constexpr (kSmem) return *claim_p(v);
+        else return __ldcg(claim_p(v));
     }
 
     __device__ void load_row(int u, int (&r)[8]) const {
-        const int4* p = a->ell + 2 * (size_t)u;
-        const int4 x = __ldg(p), y = __ldg(p + 1);
+        int4 x, y;
+        if constexpr (kSmem) {
+            const int4* p = a->ell + 2 * (size_t)(u - a->v0);
+            x = p[0];
+            y = p[1];
+        } else {
+            const int4* p = a->ell + 2 * (size_t)u;
+            x = __ldg(p);
+            y = __ldg(p + 1);
+        }
         r[0] = x.x; r[1] = x.y; r[2] = x.z; r[3] = x.w;
         r[4] = y.x; r[5] = y.y; r[6] = y.z; r[7] = y.w;
     }
@@ -342,7 +363,7 @@ struct Engine {
                     // issue every exchange before looking at any result, so they overlap
                     int old[kEllNb];
 #pragma unroll
-                    for (int k = 0; k < kEllNb; ++k) old[k] = k < d ? atomicExch(a->vis + r[k], s) : s;
+                    for (int k = 0; k < kEllNb; ++k) old[k] = k < d ? atomicExch(vis_p(r[k]), s) : s;
 #pragma unroll
                     for (int k = 0; k < kEllNb; ++k) mask |= (old[k] != s ? 1u : 0u) << k;
                 }
@@ -352,7 +373,7 @@ struct Engine {
                 const int rp = __ldg(a->rowptr + u);
                 for (int k = kEllNb; k < d; ++k) {
                     const int w = __ldg(a->adj + rp + k);
-                    if (atomicExch(a->vis + w, s) != s) {
+                    if (atomicExch(vis_p(w), s) != s) {
                         const int pos = atomicAdd(tail, 1);
                         nxt[pos] = w;
                         if (ncache && pos < kCache) ncache[pos] = w;
@@ -389,7 +410,7 @@ struct Engine {
         const int s = ++sweep_id;
         const int b = cta_rank(), B = cta_count();
         if (b == 0 && threadIdx.x == 0) {
-            a->vis[root] = s;
+            *vis_p(root) = s;
             a->qa[0] = root;
             sm->cache[0][0] = root;
             if (!kCtaOnly) c->qtail[0] = c->qtail[1] = c->qtail[2] = 0;
@@ -534,7 +555,7 @@ struct Engine {
     __device__ unsigned owned_mask(const int (&rw)[8], int dg, unsigned long long key) const {
         unsigned long long cl[kEllNb];
 #pragma unroll
-        for (int k = 0; k < kEllNb; ++k) cl[k] = k < dg ? __ldcg(a->claim + rw[k]) : ~key;
+        for (int k = 0; k < kEllNb; ++k) cl[k] = k < dg ? ld_claim(rw[k]) : ~key;
         unsigned mask = 0;
 #pragma unroll
         for (int k = 0; k < kEllNb; ++k) mask |= (cl[k] == key ? 1u : 0u) << k;
@@ -563,10 +584,10 @@ struct Engine {
             const int dg = rw[7];
 #pragma unroll
             for (int k = 0; k < kEllNb; ++k)
-                if (k < dg) atomicMin(a->claim + rw[k], key);
+                if (k < dg) atomicMin(claim_p(rw[k]), key);
             if (dg > kEllNb) {
                 const int rp = __ldg(a->rowptr + u);
-                for (int k = kEllNb; k < dg; ++k) atomicMin(a->claim + __ldg(a->adj + rp + k), key);
+                for (int k = kEllNb; k < dg; ++k) atomicMin(claim_p(__ldg(a->adj + rp + k)), key);
             }
             mk = min(mk, pack_key(dg, u));
             if (j0 == 0) {
@@ -612,7 +633,7 @@ struct Engine {
                     c = __popc(mask);
                     if (dg > kEllNb) {
                         const int rp = __ldg(a->rowptr + u);
-                        for (int k = kEllNb; k < dg; ++k) c += (__ldcg(a->claim + __ldg(a->adj + rp + k)) == key);
+                        for (int k = kEllNb; k < dg; ++k) c += (ld_claim(__ldg(a->adj + rp + k)) == key);
                     }
                 }
             }
@@ -672,7 +693,7 @@ struct Engine {
                 const int rp = __ldg(a->rowptr + u);
                 for (int k = kEllNb; k < dg; ++k) {
                     const int w = __ldg(a->adj + rp + k);
-                    if (__ldcg(a->claim + w) == key) {
+                    if (ld_claim(w) == key) {
                         dst[pos] = w;
                         if (lab_base >= 0) {
                             const int lab = lab_base + pos;
@@ -704,7 +725,7 @@ struct Engine {
         const int b = cta_rank(), B = cta_count();
         const unsigned long long slot = kCtaOnly ? 0ull : ((1ull << a->obits) - 1ull) / (unsigned long long)B;
         if (b == 0 && threadIdx.x == 0) {
-            a->claim[root] = 0;
+            *claim_p(root) = 0;
             a->perm[a->n - 1 - nv] = root;
             sm->cache[0][0] = root;
             if (!kCtaOnly) c->qtail[0] = c->qtail[1] = c->qtail[2] = 0;
@@ -885,7 +906,7 @@ struct Engine {
             if (f) {
                 const int lab = carry + ex;
                 a->perm[n - 1 - lab] = a->v0 + i;
-                a->claim[a->v0 + i] = 0;
+                *claim_p(a->v0 + i) = 0;
             }
             carry += tot;
         }
@@ -897,7 +918,7 @@ struct Engine {
         const int stride = cta_count() * blockDim.x;
         for (int i = cta_rank() * blockDim.x + threadIdx.x; i < size; i += stride) {
             const int v = ldcg(a->perm + (n - 1 - (nv + i)));
-            if (in_graph(v)) a->claim[v] = kClaimNone;
+            if (in_graph(v)) *claim_p(v) = kClaimNone;
         }
         return barrier();
     }
@@ -908,7 +929,7 @@ struct Engine {
         const int stride = cta_count() * blockDim.x;
         for (int i = cta_rank() * blockDim.x + threadIdx.x; i < a->n; i += stride) {
             const int v = a->v0 + i;
-            if (__ldcg(a->claim + v) == kClaimNone) {
+            if (ld_claim(v) == kClaimNone) {
                 const unsigned long long k = pack_key(__ldg(a->deg + v), v);
                 m = k < m ? k : m;
             }
@@ -1000,7 +1021,7 @@ struct Engine {
         const int first = cta_rank() * blockDim.x + threadIdx.x;
         for (int i = first; i < n; i += stride) {
             const int v = v0 + i;
-            if (__ldcg(a->claim + v) == kClaimNone) {
+            if (ld_claim(v) == kClaimNone) {
                 a->cc_parent[v] = v;
                 a->cc_size[v] = 0;
                 a->cc_key[v] = kKeyMax;
@@ -1010,7 +1031,7 @@ struct Engine {
         if (!barrier()) return -2;
         for (int i = first; i < n; i += stride) {
             const int v = v0 + i;
-            if (__ldcg(a->claim + v) != kClaimNone) continue;
+            if (ld_claim(v) != kClaimNone) continue;
             int r[8];
             load_row(v, r);
             const int d = r[7];
@@ -1028,7 +1049,7 @@ struct Engine {
         if (!barrier()) return -2;
         for (int i = first; i < n; i += stride) {
             const int v = v0 + i;
-            if (__ldcg(a->claim + v) != kClaimNone) continue;
+            if (ld_claim(v) != kClaimNone) continue;
             const int r = cc_root((volatile int*)a->cc_parent, v, v0, v0 + n);
             if (r < 0) fail_at(kSiteParent, v);
             if (r == v) {
@@ -1047,7 +1068,7 @@ struct Engine {
         for (int i0 = cta_rank() * blockDim.x; i0 < n; i0 += stride) {
             const int i = i0 + (int)threadIdx.x;
             const int v = v0 + i;
-            bool ok = i < n && __ldcg(a->claim + v) == kClaimNone;
+            bool ok = i < n && ld_claim(v) == kClaimNone;
             const int root = ok ? cc_root((volatile int*)a->cc_parent, v, v0, v0 + n) : -1;
             if (ok && root < 0) {
                 fail_at(kSiteParent, v);

@@ -7,10 +7,12 @@
 //    caller's buffer is in host memory), a status word and the workspace of the ordering.
 //    Requests are admitted in arrival order whenever a region and an in-flight slot are free; a
 //    request larger than the whole budget is refused at submission (RCM_ERR_TOO_LARGE).
-//  * Execution: each admitted request gets its own stream and runs as a batch of one graph: the
-//    validation and sorted-row kernels, then the batched executor with one CTA (Engine<true>,
-//    rcm_batch.cu). Requests that arrive while others are on the GPU start as soon as they are
-//    admitted and run side by side on different SMs.
+//  * Execution: each admitted request gets its own stream. Requests below kServeClusterMin
+//    vertices run as a batch of one graph: the validation and sorted-row kernels, then the batched
+//    executor with one CTA (Engine<true>, rcm_batch.cu). Larger ones run the persistent engine of
+//    rcm_order (Engine<false>) launched as one thread-block cluster, whose CTAs the hardware
+//    schedules together, so wide levels spread over several SMs. Requests that arrive while
+//    others are on the GPU start as soon as they are admitted and run side by side.
 //  * Completion: a host function enqueued after the result copy marks the request done, records
 //    its completion time and frees its region and slot; a worker thread admits waiting requests.
 //  * Failure: after a kernel fault the context is unusable and host functions behind the fault
@@ -32,11 +34,16 @@
 #include "rcm_batch.cuh"
 #include "rcm_host.hpp"
 #include "rcm_internal.cuh"
+#include "rcm_single.cuh"
 
 namespace rcm {
 
+// Requests of at least this many vertices run on a cluster by default (see the header comment).
+constexpr long long kServeClusterMin = 1LL << 18;
+
 // Arena bytes of one request: the staged CSR and result when they are in host memory, a 256-byte
-// header holding the graph offsets {0, n} of the batch of one, and the batched executor's workspace.
+// header holding the graph offsets {0, n} of a batch of one, and the larger of the two executors'
+// workspaces (so the size is plain arithmetic on n and nnz).
 static size_t request_bytes(long long n, long long nnz, bool stage_in, bool stage_out) {
     const size_t N = (size_t)std::max(n, 1LL), E = (size_t)std::max(nnz, 1LL);
     size_t o = 0;
@@ -47,7 +54,8 @@ static size_t request_bytes(long long n, long long nnz, bool stage_in, bool stag
     }
     if (stage_out) take(sizeof(int) * N);
     take(256);  // graph offsets
-    return o + batch_layout(std::max(n, 1LL), std::max(nnz, 0LL)).total;
+    const long long n1 = std::max(n, 1LL), e0 = std::max(nnz, 0LL);
+    return o + std::max(batch_layout(n1, e0).total, single_layout(n1, e0).total);
 }
 
 // First-fit allocator over [0, size) with coalescing (host-side bookkeeping of the arena).
@@ -141,6 +149,8 @@ struct Server {
     long long submitted = 0, completed = 0, failed = 0, cancelled = 0;
     int running = 0, max_running = 0;
     cudaError_t broken = cudaSuccess;  // first stream error seen: the context is unusable
+    long long cluster_min = kServeClusterMin;  // -1: never
+    int cluster_blocks = 0;                    // 0: the largest cluster the device allows
     bool trace = false;                // RCM_TRACE_ERRORS set: failed requests are reported on stderr
 };
 
@@ -198,18 +208,31 @@ static rcm_status launch_request(Server* s, Request* r) {
     }
     if (r->out_host) perm = (int*)take(sizeof(int) * N);
     long long* d_goff = (long long*)take(256);
-    const BatchLayout L = batch_layout(std::max(r->n, 1), std::max(r->nnz, 0LL));
-    char* ws = take(L.total);
+    char* ws = base + o;  // the workspace takes the rest of the region
     SlotHost* hs = &s->h_slots[r->slot];
-    hs->goff[0] = 0;
-    hs->goff[1] = r->n;
     hs->status = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_goff, hs->goff, sizeof(hs->goff), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = enqueue_batch(1, r->n, (int)r->nnz, d_goff, rowptr, colidx, perm, ws, L, st);
+    const int* status_dev = nullptr;
+    if (s->cluster_min >= 0 && r->n >= s->cluster_min && single_cluster_max() > 0) {
+        const SingleLayout L = single_layout(r->n, r->nnz);
+        rcm_options o{};
+        o.cluster = 1;
+        o.grid_blocks = s->cluster_blocks;
+        SingleLaunch sl;
+        const rcm_status ls = single_launch(r->n, o, &sl);
+        if (ls != RCM_OK) return ls;
+        if (e == cudaSuccess) e = enqueue_single(r->n, r->nnz, rowptr, colidx, perm, ws, L, sl, nullptr, st);
+        status_dev = (const int*)(ws + L.ctl + offsetof(Ctl, status));
+    } else {
+        const BatchLayout L = batch_layout(std::max(r->n, 1), std::max(r->nnz, 0LL));
+        hs->goff[0] = 0;
+        hs->goff[1] = r->n;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_goff, hs->goff, sizeof(hs->goff), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = enqueue_batch(1, r->n, (int)r->nnz, d_goff, rowptr, colidx, perm, ws, L, st);
+        status_dev = (const int*)(ws + L.ctl + offsetof(Ctl, status));
+    }
     if (e == cudaSuccess && r->out_host)
         e = cudaMemcpyAsync(r->perm, perm, sizeof(int) * (size_t)r->n, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&hs->status, ws + L.ctl + offsetof(Ctl, status), sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hs->status, status_dev, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaLaunchHostFunc(st, on_request_done, r);
     return e == cudaSuccess ? RCM_OK : cuda_status(e);
 }
@@ -335,8 +358,16 @@ size_t rcm_request_bytes(int32_t n, int64_t nnz, int32_t host_csr, int32_t host_
 }
 
 rcm_status rcm_server_create(size_t hbm_budget_bytes, int32_t max_inflight, rcm_server** out) {
+    return rcm_server_create_ex(hbm_budget_bytes, max_inflight, nullptr, out);
+}
+
+rcm_status rcm_server_create_ex(size_t hbm_budget_bytes, int32_t max_inflight, const rcm_server_options* opts,
+                                rcm_server** out) {
     if (!out || hbm_budget_bytes == 0 || max_inflight <= 0 || max_inflight > 4096) return RCM_ERR_INVALID_ARG;
     *out = nullptr;
+    if (opts && (opts->cluster_min_vertices < -1 || opts->cluster_blocks < 0 || opts->cluster_blocks > 16 ||
+                 opts->cluster_blocks == 1))
+        return RCM_ERR_INVALID_ARG;
     rcm_server* srv = new (std::nothrow) rcm_server();
     if (!srv) return RCM_ERR_OOM;
     Server& s = srv->s;
@@ -356,6 +387,10 @@ rcm_status rcm_server_create(size_t hbm_budget_bytes, int32_t max_inflight, rcm_
     }
     s.alloc.reset(s.budget);
     s.max_inflight = max_inflight;
+    if (opts) {
+        s.cluster_min = opts->cluster_min_vertices == 0 ? kServeClusterMin : opts->cluster_min_vertices;
+        s.cluster_blocks = opts->cluster_blocks;
+    }
     s.slot_req.assign(max_inflight, nullptr);
     s.trace = std::getenv("RCM_TRACE_ERRORS") != nullptr;
     s.streams.resize(max_inflight);

@@ -6,6 +6,7 @@
 
 #include "rcm_host.hpp"
 #include "rcm_engine.cuh"
+#include "rcm_single.cuh"
 #include "rcm_internal.cuh"
 #include "rcm_prep.cuh"
 
@@ -127,6 +128,53 @@ __global__ void __launch_bounds__(kThreads, 1) k_rcm_single(EngineArgs args, int
 }
 
 
+// Graphs of at most kSmallMaxN vertices: one CTA orders the whole graph with its claims, visit
+// stamps and padded rows in shared memory (Engine<true, true>), so every level's row reads and
+// atomics stay inside one SM instead of going to L2.
+constexpr int kSmallMaxN = 4608;
+constexpr int kSmallThreads = 512;
+constexpr int kSmallSort = 256;  // component tables sorted in shared memory up to this size
+
+// Shared-memory layout: claims (8n bytes) at 0, stamps (4n) and then the padded rows (32n, read
+// and written as 16-byte int4) each at the next 16-byte boundary.
+static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+static size_t small_vis_off(int n) { return align16(8 * (size_t)n); }
+static size_t small_ell_off(int n) { return align16(small_vis_off(n) + 4 * (size_t)n); }
+static size_t small_smem_bytes(int n) { return small_ell_off(n) + 32 * (size_t)n; }
+
+__global__ void __launch_bounds__(kSmallThreads, 1) k_rcm_small(EngineArgs args, int vis_off, int ell_off) {
+    extern __shared__ __align__(16) unsigned long long s_state[];
+    __shared__ EngineSmem smem;
+    __shared__ unsigned long long s_sort[kSmallSort + kSmallSort / 2];
+    Ctl* ctl = args.ctl;
+    if (ld_volatile(&ctl->status) & kErrBadCsr) return;
+    const int n = args.n;
+    unsigned long long* claim = s_state;
+    int* vis = (int*)((char*)s_state + vis_off);
+    int4* ell = (int4*)((char*)s_state + ell_off);
+    for (int i = threadIdx.x; i < n; i += kSmallThreads) {
+        claim[i] = kClaimNone;
+        vis[i] = 0;
+        ell[2 * i] = __ldg(args.ell + 2 * (size_t)i);
+        ell[2 * i + 1] = __ldg(args.ell + 2 * (size_t)i + 1);
+    }
+    __syncthreads();
+    EngineArgs a = args;
+    a.claim = claim;
+    a.vis = vis;
+    a.ell = ell;
+    Engine<true, true> e;
+    e.init(a, &smem);
+    e.sm_sort = s_sort;
+    e.sm_sort_cap = kSmallSort;
+    e.run();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 8; ++i) ctl->stats[i] = smem.st[i];
+        for (int i = 0; i < 8; ++i) ctl->phase_ns[i] = smem.prof[i];
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 // host side
 
@@ -134,14 +182,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_rcm_single(EngineArgs args, int
 // CTA each, concurrently.
 constexpr int kComponentOnGrid = 1 << 18;
 
-struct SingleLayout {
-    size_t ctl, pool4, deg, claim, vis, bigrows, adj, ell, cc_size, cc_key, cc_roots, cc_gkey, cc_gidx, cc_tab, total;
-    int cc_cap;
-};
-
 // with_cc: also the arrays of the concurrent-components pass (the fixed no-allocation workspace
 // leaves them out and orders components one by one).
-static SingleLayout single_layout(long long n, long long nnz, bool with_cc = true) {
+SingleLayout single_layout(long long n, long long nnz, bool with_cc) {
     SingleLayout L;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -218,34 +261,101 @@ static int single_blocks_per_sm(int threads) {
     return g_single_blocks_per_sm[idx];
 }
 
-rcm_status order_single(int32_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colidx,
-                        int32_t* perm, const rcm_options* opts, long long* stats_dev, cudaEvent_t* ev,
-                        cudaStream_t s) {
+static int g_cluster_max = -1;
+
+int single_cluster_max() {
+    if (single_blocks_per_sm(512) <= 0) return 0;
+    std::lock_guard<std::mutex> g(g_single_mu);
+    if (g_cluster_max < 0) {
+        g_cluster_max = 0;
+        const void* k = single_kernel(512);
+        cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        for (int c : {16, 8}) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(c);
+            cfg.blockDim = dim3(512);
+            cfg.dynamicSmemBytes = kSingleDynSmem;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = c;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int clusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&clusters, k, &cfg) == cudaSuccess && clusters > 0) {
+                g_cluster_max = c;
+                break;
+            }
+            cudaGetLastError();
+        }
+    }
+    return g_cluster_max;
+}
+
+static std::once_flag g_small_once;
+static cudaError_t g_small_attr = cudaSuccess;
+
+rcm_status single_launch(int n, const rcm_options& o, SingleLaunch* out) {
     const DeviceInfo& di = device_info();
-    rcm_options o{};
-    if (opts) o = *opts;
-    const int threads = o.block_threads ? o.block_threads : 512;
-    if (threads_index(threads) < 0) return RCM_ERR_INVALID_ARG;
-    const int per_sm = single_blocks_per_sm(threads);
+    SingleLaunch sl;
+    // the shared-memory CTA engine: on request, or automatically for small graphs when no option
+    // shapes the persistent grid
+    const bool defaults = o.grid_blocks == 0 && o.cluster == 0 && o.narrow_threshold == 0 &&
+                          (o.block_threads == 0 || o.block_threads == kSmallThreads) && o.debug_stall_barrier == 0;
+    if (o.executor == 2 || (o.executor == 0 && defaults && n <= kSmallMaxN)) {
+        if (n > kSmallMaxN) return RCM_ERR_TOO_LARGE;
+        std::call_once(g_small_once, [] {
+            g_small_attr = cudaFuncSetAttribute(k_rcm_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)small_smem_bytes(kSmallMaxN));
+        });
+        if (g_small_attr != cudaSuccess) return RCM_ERR_CUDA;
+        single_blocks_per_sm(kSmallThreads);  // sets up the preprocessing kernels' attributes
+        sl.small = true;
+        sl.threads = kSmallThreads;
+        sl.blocks = 1;
+        sl.fused = o.fused_sweeps >= 0 ? 1 : 0;
+        sl.profile = o.profile_phases ? 1 : 0;
+        *out = sl;
+        return RCM_OK;
+    }
+    sl.threads = o.block_threads ? o.block_threads : 512;
+    if (threads_index(sl.threads) < 0) return RCM_ERR_INVALID_ARG;
+    const int per_sm = single_blocks_per_sm(sl.threads);
     if (per_sm <= 0) return RCM_ERR_CUDA;
-    const int max_blocks = std::min(per_sm * di.sms, kMaxGridBlocks);
-    int blocks = o.grid_blocks ? o.grid_blocks : di.sms;
-    if (blocks < 1 || blocks > max_blocks) return RCM_ERR_INVALID_ARG;
+    sl.cluster = o.cluster != 0;
+    if (sl.cluster) {
+        // one cluster: only the 512-thread engine is set up for it
+        const int cmax = sl.threads == 512 ? single_cluster_max() : 0;
+        sl.blocks = o.grid_blocks ? o.grid_blocks : cmax;
+        if (cmax == 0 || sl.blocks < 1 || sl.blocks > cmax) return RCM_ERR_INVALID_ARG;
+    } else {
+        const int max_blocks = std::min(per_sm * di.sms, kMaxGridBlocks);
+        sl.blocks = o.grid_blocks ? o.grid_blocks : di.sms;
+        if (sl.blocks < 1 || sl.blocks > max_blocks) return RCM_ERR_INVALID_ARG;
+    }
     // claim keys: (level + 1) in the high bits, the in-level order b * slot + j in the low obits;
     // slot = (2^obits - 1) / blocks must exceed any slice size (< n)
     const int obits = claim_order_bits(n);
     const unsigned long long slot_cap = ((1ull << obits) - 1ull) / (unsigned long long)std::max(n, 1);
-    if ((unsigned long long)blocks > slot_cap) blocks = (int)std::max(1ull, slot_cap);
+    if ((unsigned long long)sl.blocks > slot_cap) {
+        if (sl.cluster) return RCM_ERR_TOO_LARGE;
+        sl.blocks = (int)std::max(1ull, slot_cap);
+    }
     // narrow runs keep the frontier in a shared-memory cache of kCache ids
-    int narrow = o.narrow_threshold == 0 ? 2 * threads : (o.narrow_threshold < 0 ? 0 : o.narrow_threshold);
-    narrow = std::min(narrow, kCache);
-    const long long limit = o.spin_limit_ns > 0 ? o.spin_limit_ns : 20000000000LL;
+    int narrow = o.narrow_threshold == 0 ? 2 * sl.threads : (o.narrow_threshold < 0 ? 0 : o.narrow_threshold);
+    sl.narrow = std::min(narrow, kCache);
+    sl.limit_ns = o.spin_limit_ns > 0 ? o.spin_limit_ns : 20000000000LL;
+    sl.fused = o.fused_sweeps >= 0 ? 1 : 0;
+    sl.profile = o.profile_phases ? 1 : 0;
+    sl.stall = o.debug_stall_barrier ? 1 : 0;
+    *out = sl;
+    return RCM_OK;
+}
 
-    const SingleLayout L = single_layout(n, nnz);
-    void* ws = nullptr;
-    rcm_status st = ws_alloc(&ws, L.total, s);
-    if (st != RCM_OK) return st;
-    char* base = (char*)ws;
+cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* colidx, int* perm, char* base,
+                           const SingleLayout& L, const SingleLaunch& sl, cudaEvent_t* ev, cudaStream_t s) {
+    const DeviceInfo& di = device_info();
     Ctl* ctl = (Ctl*)(base + L.ctl);
     int* pool4 = (int*)(base + L.pool4);
     int* deg = (int*)(base + L.deg);
@@ -271,26 +381,29 @@ rcm_status order_single(int32_t n, int64_t nnz, const int32_t* rowptr, const int
         e = cudaGetLastError();
         if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
     }
-    if (e == cudaSuccess) {
-        EngineArgs args;
-        args.n = n;
-        args.v0 = 0;
-        args.rowptr = rowptr;
-        args.ell = ell;
-        args.adj = adj;
-        args.deg = deg;
-        args.claim = claim;
-        args.vis = vis;
-        args.qa = pool4;
-        args.qb = pool4 + n;
-        args.boff = pool4 + 2 * (size_t)n;
-        args.perm = perm;
-        args.ctl = ctl;
-        args.status = &ctl->status;
-        args.diag = nullptr;
-        args.narrow_thr = narrow;
-        args.obits = obits;
-        args.profile = o.profile_phases ? 1 : 0;
+    if (e != cudaSuccess) return e;
+    EngineArgs args;
+    args.n = n;
+    args.v0 = 0;
+    args.rowptr = rowptr;
+    args.ell = ell;
+    args.adj = adj;
+    args.deg = deg;
+    args.claim = claim;
+    args.vis = vis;
+    args.qa = pool4;
+    args.qb = pool4 + n;
+    args.boff = pool4 + 2 * (size_t)n;
+    args.perm = perm;
+    args.ctl = ctl;
+    args.status = &ctl->status;
+    args.diag = nullptr;
+    args.narrow_thr = sl.narrow;
+    args.obits = claim_order_bits(n);
+    args.profile = sl.profile;
+    args.fused = sl.fused;
+    args.limit_ns = sl.limit_ns;
+    if (L.cc_cap > 0) {
         args.cc_parent = pool4 + 3 * (size_t)n;
         args.cc_size = (int*)(base + L.cc_size);
         args.cc_key = (unsigned long long*)(base + L.cc_key);
@@ -298,16 +411,55 @@ rcm_status order_single(int32_t n, int64_t nnz, const int32_t* rowptr, const int
         args.cc_gkey = (unsigned long long*)(base + L.cc_gkey);
         args.cc_gidx = (int*)(base + L.cc_gidx);
         args.cc_tab = (int4*)(base + L.cc_tab);
-        args.cc_cap = L.cc_cap;
-        args.cc_big = kComponentOnGrid;
-        args.fused = o.fused_sweeps >= 0 ? 1 : 0;
-        args.limit_ns = limit;
-        int stall = o.debug_stall_barrier ? 1 : 0;
-        void* kargs[] = {&args, &stall};
-        e = cudaLaunchCooperativeKernel(single_kernel(threads), dim3(blocks), dim3(threads), kargs, kSingleDynSmem, s);
-        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
+    } else {
+        args.cc_parent = args.cc_size = args.cc_roots = args.cc_gidx = nullptr;
+        args.cc_key = args.cc_gkey = nullptr;
+        args.cc_tab = nullptr;
     }
-    if (e == cudaSuccess) e = enqueue_latch(ctl, stream_latch(s), stats_dev, s);
+    args.cc_cap = L.cc_cap;
+    args.cc_big = kComponentOnGrid;
+    int stall = sl.stall;
+    void* kargs[] = {&args, &stall};
+    if (sl.small) {
+        k_rcm_small<<<1, kSmallThreads, small_smem_bytes(n), s>>>(args, (int)small_vis_off(n), (int)small_ell_off(n));
+        e = cudaGetLastError();
+    } else if (sl.cluster) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(sl.blocks);
+        cfg.blockDim = dim3(sl.threads);
+        cfg.dynamicSmemBytes = kSingleDynSmem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = sl.blocks;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelExC(&cfg, single_kernel(sl.threads), kargs);
+    } else {
+        e = cudaLaunchCooperativeKernel(single_kernel(sl.threads), dim3(sl.blocks), dim3(sl.threads), kargs,
+                                        kSingleDynSmem, s);
+    }
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
+    return e;
+}
+
+rcm_status order_single(int32_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colidx,
+                        int32_t* perm, const rcm_options* opts, long long* stats_dev, cudaEvent_t* ev,
+                        cudaStream_t s) {
+    rcm_options o{};
+    if (opts) o = *opts;
+    SingleLaunch sl;
+    rcm_status st = single_launch(n, o, &sl);
+    if (st != RCM_OK) return st;
+    const SingleLayout L = single_layout(n, nnz);
+    void* ws = nullptr;
+    st = ws_alloc(&ws, L.total, s);
+    if (st != RCM_OK) return st;
+    char* base = (char*)ws;
+    cudaError_t e = enqueue_single(n, nnz, rowptr, colidx, perm, base, L, sl, ev, s);
+    if (e == cudaSuccess) e = enqueue_latch((Ctl*)(base + L.ctl), stream_latch(s), stats_dev, s);
     ws_free(ws, s);
     return e == cudaSuccess ? RCM_OK : cuda_status(e);
 }
@@ -381,70 +533,14 @@ rcm_status order_single_noalloc(int32_t n, const int32_t* rowptr, const int32_t*
     const SingleLayout L = single_layout(n, nnz, false);
     if (L.total > kNoAllocBytes) return RCM_ERR_TOO_LARGE;
 
-    const DeviceInfo& di = device_info();
-    const int threads = 512;
-    const int per_sm = single_blocks_per_sm(threads);
-    if (per_sm <= 0) return RCM_ERR_CUDA;
-    int blocks = std::min(di.sms, std::min(per_sm * di.sms, kMaxGridBlocks));
-    const int obits = claim_order_bits(n);
-    const unsigned long long slot_cap = ((1ull << obits) - 1ull) / (unsigned long long)std::max(n, 1);
-    if ((unsigned long long)blocks > slot_cap) blocks = (int)std::max(1ull, slot_cap);
-
+    SingleLaunch sl;
+    st = single_launch(n, rcm_options{}, &sl);
+    if (st != RCM_OK) return st;
     char* base = (char*)ws;
     Ctl* ctl = (Ctl*)(base + L.ctl);
-    int* pool4 = (int*)(base + L.pool4);
-    int* deg = (int*)(base + L.deg);
-    unsigned long long* claim = (unsigned long long*)(base + L.claim);
-    int* vis = (int*)(base + L.vis);
-    int* bigrows = (int*)(base + L.bigrows);
-    int* adj = (int*)(base + L.adj);
-    int4* ell = (int4*)(base + L.ell);
-    // the array keeps the previous call's contents: the control block must start at zero; every
-    // other per-vertex array is initialised by the kernels below
-    e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), s);
-    if (e == cudaSuccess) {
-        const int pb = 256;
-        const int pgrid = (int)std::min<long long>((n + pb - 1) / pb, (long long)di.sms * 16);
-        k_degree_validate<<<std::max(pgrid, 1), pb, 0, s>>>(n, (int)nnz, rowptr, colidx, deg, claim, vis, bigrows, ctl,
-                                                           kSmallRowMax);
-        k_sort_rows_small<<<std::max(pgrid, 1), pb, 0, s>>>(n, rowptr, colidx, deg, adj, ell, ctl);
-        // rows longer than kSmallRowMax entries number at most nnz / (kSmallRowMax + 1)
-        const int big_grid = (int)std::max<long long>(1, std::min<long long>(2LL * di.sms, nnz / (kSmallRowMax + 1)));
-        k_sort_rows_big<<<big_grid, 1024, sizeof(unsigned long long) * kBigRowSmem, s>>>(
-            n, rowptr, colidx, deg, adj, ell, bigrows, ctl, (unsigned long long*)pool4);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) {
-        EngineArgs args;
-        args.n = n;
-        args.v0 = 0;
-        args.rowptr = rowptr;
-        args.ell = ell;
-        args.adj = adj;
-        args.deg = deg;
-        args.claim = claim;
-        args.vis = vis;
-        args.qa = pool4;
-        args.qb = pool4 + n;
-        args.boff = pool4 + 2 * (size_t)n;
-        args.perm = perm;
-        args.ctl = ctl;
-        args.status = &ctl->status;
-        args.diag = nullptr;
-        args.narrow_thr = std::min(2 * threads, kCache);
-        args.obits = obits;
-        args.profile = 0;
-        args.fused = 1;
-        args.limit_ns = 20000000000LL;
-        args.cc_parent = args.cc_size = args.cc_roots = args.cc_gidx = nullptr;
-        args.cc_key = args.cc_gkey = nullptr;
-        args.cc_tab = nullptr;
-        args.cc_cap = 0;
-        args.cc_big = 0;
-        int stall = 0;
-        void* kargs[] = {&args, &stall};
-        e = cudaLaunchCooperativeKernel(single_kernel(threads), dim3(blocks), dim3(threads), kargs, kSingleDynSmem, s);
-    }
+    // the array keeps the previous call's contents: enqueue_single clears the control block, and
+    // its kernels initialise every per-vertex array they read
+    e = enqueue_single(n, nnz, rowptr, colidx, perm, base, L, sl, nullptr, s);
     // synchronous: the device-detected status is read back from the control block
     int bits = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, &ctl->status, sizeof(int), cudaMemcpyDeviceToHost, s);

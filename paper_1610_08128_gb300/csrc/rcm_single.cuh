@@ -1,0 +1,48 @@
+// rcm_single.cuh -- host-side pieces of the one-graph path (the persistent engine of
+// rcm_single.cu), shared by rcm_order and the serving path.
+#pragma once
+
+#include "rcm_internal.cuh"
+
+namespace rcm {
+
+// Byte offsets of the one-graph workspace, each 256-byte aligned; total = bytes to allocate.
+// cc_cap = components the concurrent-components pass handles (0 = that pass is off and the
+// component arrays are absent).
+struct SingleLayout {
+    size_t ctl, pool4, deg, claim, vis, bigrows, adj, ell, cc_size, cc_key, cc_roots, cc_gkey, cc_gidx, cc_tab, total;
+    int cc_cap;
+};
+SingleLayout single_layout(long long n, long long nnz, bool with_cc = true);
+
+// Launch shape of the engine.
+//   small = true:    one CTA holding the graph's claims, stamps and rows in shared memory.
+//   cluster = false: a cooperative grid of `blocks` CTAs (at most the co-resident limit).
+//   cluster = true:  one thread-block cluster of `blocks` CTAs (2..16); the hardware schedules a
+//                    cluster's CTAs together, so they are co-resident whatever else runs.
+struct SingleLaunch {
+    int threads = 512;
+    int blocks = 0;
+    bool cluster = false;
+    bool small = false;          // one CTA with the graph's state in shared memory (k_rcm_small)
+    int narrow = 0;              // frontier size below which CTA 0 runs levels alone
+    long long limit_ns = 20000000000LL;
+    int fused = 1;
+    int profile = 0;
+    int stall = 0;
+};
+
+// Derives the launch shape from options for a graph of n vertices; RCM_ERR_INVALID_ARG for
+// unsupported shapes.
+rcm_status single_launch(int n, const rcm_options& o, SingleLaunch* out);
+
+// Largest cluster the engine can be launched as on this device (16 or 8), 0 if none.
+int single_cluster_max();
+
+// Enqueues on s, with the workspace at base (laid out by single_layout): control-block reset,
+// degrees and checks (rowptr[n] == nnz), sorted rows, then the persistent engine. ev (optional):
+// three events recorded before preprocessing, before the engine and after it.
+cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* colidx, int* perm, char* base,
+                           const SingleLayout& L, const SingleLaunch& sl, cudaEvent_t* ev, cudaStream_t s);
+
+}  // namespace rcm

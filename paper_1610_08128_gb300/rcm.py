@@ -38,8 +38,14 @@ class rcm_options(ctypes.Structure):
         ("nnz", ctypes.c_int64),
         ("debug_stall_barrier", ctypes.c_int32),
         ("profile_phases", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("cluster", ctypes.c_int32),
+        ("executor", ctypes.c_int32),
     ]
+
+
+class rcm_server_options(ctypes.Structure):
+    _fields_ = [("cluster_min_vertices", ctypes.c_int64), ("cluster_blocks", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class rcm_stats(ctypes.Structure):
@@ -92,6 +98,7 @@ def load():
         "rcm_bandwidth_profile": ([I32, P, P, P, ctypes.POINTER(I64), ctypes.POINTER(I64), P], ctypes.c_int),
         "rcm_request_bytes": ([I32, I64, I32, I32], SZ),
         "rcm_server_create": ([SZ, I32, ctypes.POINTER(P)], ctypes.c_int),
+        "rcm_server_create_ex": ([SZ, I32, ctypes.POINTER(rcm_server_options), ctypes.POINTER(P)], ctypes.c_int),
         "rcm_submit": ([P, I32, I64, P, P, P, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
         "rcm_poll": ([P, ctypes.c_uint64], ctypes.c_int),
         "rcm_wait": ([P, ctypes.c_uint64], ctypes.c_int),
@@ -197,6 +204,14 @@ def rcm_bandwidth_profile(n, rowptr, colidx, perm, stream=None):
 
 def rcm_request_bytes(n, nnz, host_csr=True, host_out=True) -> int:
     return int(load().rcm_request_bytes(int(n), int(nnz), int(bool(host_csr)), int(bool(host_out))))
+
+
+def rcm_server_create_ex(hbm_budget_bytes, max_inflight, options=None):
+    """Returns (status, server handle); options: rcm_server_options or None."""
+    h = ctypes.c_void_p()
+    st = load().rcm_server_create_ex(int(hbm_budget_bytes), int(max_inflight),
+                                     ctypes.byref(options) if options is not None else None, ctypes.byref(h))
+    return st, h
 
 
 def rcm_server_create(hbm_budget_bytes, max_inflight):

@@ -150,6 +150,10 @@ OPTION_SETS = [
     {"block_threads": 512, "narrow_threshold": 100},
     {"fused_sweeps": -1},
     {"fused_sweeps": -1, "narrow_threshold": -1},
+    {"cluster": 1},                      # one thread-block cluster, the largest the device allows
+    {"cluster": 1, "grid_blocks": 8},
+    {"cluster": 1, "grid_blocks": 2, "narrow_threshold": -1},
+    {"executor": 1},                     # persistent grid even for graphs the shared-memory CTA takes
 ]
 
 
@@ -159,6 +163,34 @@ def test_options_do_not_change_the_result(opts):
               synth.random_graph(3000, 4000, 9)] + small_graphs(25, 200, 102)
     for g in graphs:
         assert_parity(g, opts)
+
+
+def test_shared_memory_executor_matches_oracle():
+    """One CTA with the graph's claims, stamps and padded rows in shared memory (graphs of at most
+    4,608 vertices): the same orders as the oracle and the persistent grid, on grids, meshes with
+    components, trees, stars with long rows, isolated vertices and random graphs."""
+    graphs = [synth.c1_grid2d(), synth.grid((16, 16, 18), seed=5), synth.c3_mesh(4608, seed_offset=2),
+              synth.path(4608), synth.random_tree(4000, 6), synth.csr_from_edges(300, [], []),
+              synth.csr_from_edges(5, [0, 1], [1, 2])]
+    star_src = np.zeros(999, np.int64)
+    graphs.append(synth.csr_from_edges(1000, star_src, np.arange(1, 1000)))   # a 999-entry row
+    graphs += small_graphs(40, 600, 108)
+    for g in graphs:
+        assert g.n <= 4608
+        assert_parity(g, {"executor": 2})
+        assert np.array_equal(gpu_perm(g, {"executor": 2}), gpu_perm(g, {"executor": 1}))
+
+
+def test_shared_memory_executor_limits():
+    rcm = rcm_mod()
+    g = synth.grid((4609, 1), seed=1)
+    rp, ci = to_dev(g)
+    perm = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    o = rcm.rcm_options()
+    o.executor = 2
+    assert rcm.rcm_order_ex(g.n, rp, ci, perm, o, None) == rcm.RCM_ERR_TOO_LARGE
+    o.executor = 3
+    assert rcm.rcm_order_ex(g.n, rp, ci, perm, o, None) == rcm.RCM_ERR_INVALID_ARG
 
 
 def test_stats_match_oracle():
@@ -205,6 +237,10 @@ def test_invalid_arguments():
     o = rcm.rcm_options()
     o.grid_blocks = 100000
     assert rcm.rcm_order_ex(g.n, rp, ci, perm, o, None) == rcm.RCM_ERR_INVALID_ARG
+    for cluster, blocks, threads in [(2, 0, 0), (1, 0, 256), (1, 17, 0)]:
+        o = rcm.rcm_options()
+        o.cluster, o.grid_blocks, o.block_threads = cluster, blocks, threads
+        assert rcm.rcm_order_ex(g.n, rp, ci, perm, o, None) == rcm.RCM_ERR_INVALID_ARG
 
 
 def test_bounded_wait_reports_timeout():

@@ -73,6 +73,37 @@ def test_served_results_equal_single_calls(rcm):
         rcm.check(rcm.rcm_server_destroy(srv), "destroy")
 
 
+def test_large_requests_run_on_a_cluster(rcm):
+    """Requests of 2^18 vertices or more run the persistent engine launched as one thread-block
+    cluster, mixed with small requests on single CTAs; every result equals the oracle and
+    rcm_order alone."""
+    big = [synth.grid((70, 70, 70), seed=11), synth.grid((600, 600), seed=12),
+           synth.batch_graph(2, 300000, [503, 0])]
+    small = mix(9, 503)
+    graphs = [g for pair in zip(big, small[0::3]) for g in pair] + small[1::3] + small[2::3]
+    st, srv = rcm.rcm_server_create(8 << 30, 32)
+    rcm.check(st, "create")
+    try:
+        outs, ins, tickets = [], [], []
+        for g in graphs:
+            o = torch.empty(g.n, dtype=torch.int32).pin_memory()
+            rp, ci = torch.from_numpy(g.rowptr).pin_memory(), torch.from_numpy(g.colidx).pin_memory()
+            s, t = rcm.rcm_submit(srv, g.n, g.nnz, rp, ci, o)
+            rcm.check(s, "submit")
+            ins.append((rp, ci))   # inputs stay valid until the request finishes
+            outs.append(o)
+            tickets.append(t)
+        for g, t, o in zip(graphs, tickets, outs):
+            rcm.check(rcm.rcm_wait(srv, t), "wait")
+            assert np.array_equal(o.numpy(), oracle.rcm(g.n, g.rowptr, g.colidx))
+        for g, o in zip(big, outs[0::2][:len(big)]):
+            assert np.array_equal(o.numpy(), alone(rcm, g))
+        _, info = rcm.rcm_server_info(srv)
+        assert info["failed"] == 0 and info["max_running"] > 1
+    finally:
+        rcm.check(rcm.rcm_server_destroy(srv), "destroy")
+
+
 def test_admission_under_a_small_budget(rcm):
     graphs = mix(12, 502, lo=20000, hi=40000)
     need = max(region_bytes(g) for g in graphs)
