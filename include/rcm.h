@@ -87,7 +87,8 @@ typedef struct {
                                   above at their defaults, run on one CTA that keeps the graph's
                                   traversal state in shared memory; others on the persistent grid.
                                   1 = always the persistent grid. 2 = always the shared-memory CTA
-                                  (RCM_ERR_TOO_LARGE above 4,608 vertices)                          */
+                                  (RCM_ERR_TOO_LARGE above 4,608 vertices); with 2, block_threads
+                                  (32..512, 0 = automatic) sets that CTA's width                     */
 } rcm_options;
 
 /* Statistics of one ordering (filled by rcm_order_ex when requested). */
@@ -156,6 +157,39 @@ rcm_status rcm_order_host(int32_t n, const int32_t *rowptr, const int32_t *colid
 rcm_status rcm_order_batch(int32_t G, int64_t n_total, const int64_t *goff, const int32_t *rowptr,
                            const int32_t *colidx, int32_t *perm_out, rcm_stream_t stream);
 
+/* Tuning of the batched path (every value gives the same permutations; only speed differs). */
+typedef struct {
+    int32_t block_threads;   /* threads per CTA of the batched executor: 128, 256 or 512; 0 = 256   */
+    int32_t row_sort_split;  /* rows with at most this many stored entries are sorted by one thread,
+                                longer rows by a whole CTA: 4..32; 0 = 32                          */
+    int32_t reserved[6];
+} rcm_batch_options;
+
+/* rcm_order_batch with tuning options (opts may be NULL = defaults). RCM_ERR_INVALID_ARG for
+   values outside the ranges above. */
+rcm_status rcm_order_batch_ex(int32_t G, int64_t n_total, const int64_t *goff, const int32_t *rowptr,
+                              const int32_t *colidx, int32_t *perm_out, const rcm_batch_options *opts,
+                              rcm_stream_t stream);
+
+/*
+ * Batched replay plan: the launches of rcm_order_batch_ex for fixed device buffers, captured once
+ * into a CUDA graph with a workspace of their own, then replayed with one launch. Each replay
+ * orders whatever pattern the buffers hold at that time; it must keep G, n_total and
+ * rowptr[n_total] == nnz (a different stored-entry count is reported as RCM_ERR_BAD_CSR).
+ *   create   goff, rowptr, colidx, perm_out: device buffers as for rcm_order_batch, kept by the
+ *            caller for the plan's lifetime. Allocates the workspace; synchronous.
+ *   launch   enqueues one replay on `stream` (asynchronous).
+ *   status   synchronises `stream` and returns the device-detected status of the last replay.
+ *   destroy  frees the graph and the workspace (after synchronising the device).
+ */
+typedef struct rcm_batch_plan rcm_batch_plan;
+rcm_status rcm_batch_plan_create(int32_t G, int64_t n_total, int64_t nnz, const int64_t *goff,
+                                 const int32_t *rowptr, const int32_t *colidx, int32_t *perm_out,
+                                 const rcm_batch_options *opts, rcm_batch_plan **out);
+rcm_status rcm_batch_plan_launch(rcm_batch_plan *plan, rcm_stream_t stream);
+rcm_status rcm_batch_plan_status(rcm_batch_plan *plan, rcm_stream_t stream);
+rcm_status rcm_batch_plan_destroy(rcm_batch_plan *plan);
+
 /*
  * rcm_order_noalloc -- rcm_order for callers that must not allocate device memory (the paper has
  * no counterpart). Typical callers: an application whose memory framework has already reserved
@@ -216,7 +250,7 @@ typedef struct {
     int64_t cluster_min_vertices; /* requests of at least this many vertices run the persistent
                                      engine of rcm_order launched as one thread-block cluster;
                                      smaller ones run on one CTA. 0 = 262,144; -1 = never         */
-    int32_t cluster_blocks;       /* CTAs of that cluster, 2..16 as the device allows; 0 = largest */
+    int32_t cluster_blocks;       /* CTAs of that cluster, 2..16 as the device allows; 0 = 4       */
     int32_t reserved[5];
 } rcm_server_options;
 

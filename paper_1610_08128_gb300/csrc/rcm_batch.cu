@@ -131,25 +131,53 @@ BatchLayout batch_layout(long long n_total, long long nnz) {
 }
 
 static std::mutex g_batch_mu;
-static int g_batch_per_sm = -1;
+static int g_batch_per_sm[3] = {-1, -1, -1};  // CTAs per SM of the 128-, 256- and 512-thread executor
 
-static int batch_blocks_per_sm() {
+static int batch_index(int threads) { return threads == 128 ? 0 : threads == 256 ? 1 : threads == 512 ? 2 : -1; }
+
+static const void* batch_kernel(int threads) {
+    switch (threads) {
+        case 128: return (const void*)k_rcm_batch<128>;
+        case 512: return (const void*)k_rcm_batch<512>;
+    }
+    return (const void*)k_rcm_batch<256>;
+}
+
+static int batch_blocks_per_sm(int threads) {
+    const int idx = batch_index(threads);
+    if (idx < 0) return 0;
     std::lock_guard<std::mutex> g(g_batch_mu);
-    if (g_batch_per_sm < 0) {
+    if (g_batch_per_sm[idx] < 0) {
         int bps = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_rcm_batch<256>, 256, 0);
-        g_batch_per_sm = bps;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch_kernel(threads), threads, 0);
+        g_batch_per_sm[idx] = bps;
         cudaFuncSetAttribute(k_sort_rows_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(unsigned long long) * kBigRowSmem));
     }
-    return g_batch_per_sm;
+    return g_batch_per_sm[idx];
+}
+
+rcm_status batch_tuning(const rcm_batch_options* o, BatchTuning* out) {
+    BatchTuning t;
+    if (o) {
+        if (o->block_threads) t.threads = o->block_threads;
+        if (o->row_sort_split) t.small_max = o->row_sort_split;
+    }
+    if (batch_index(t.threads) < 0 || t.small_max < 4 || t.small_max > kSmallRowMax) return RCM_ERR_INVALID_ARG;
+    *out = t;
+    return RCM_OK;
+}
+
+bool batch_prepare(const BatchTuning& t) {
+    device_info();
+    return batch_blocks_per_sm(t.threads) > 0;
 }
 
 cudaError_t enqueue_batch(int G, long long n_total, int nnz, const long long* goff, const int* rowptr,
-                          const int* colidx, int* perm, char* base, const BatchLayout& L, cudaStream_t s) {
-    constexpr int kThreads = 256;
+                          const int* colidx, int* perm, char* base, const BatchLayout& L, const BatchTuning& t,
+                          cudaStream_t s) {
     const DeviceInfo& di = device_info();
-    const int per_sm = batch_blocks_per_sm();
+    const int per_sm = batch_blocks_per_sm(t.threads);
     if (per_sm <= 0) return cudaErrorInvalidConfiguration;
     const long long N = std::max<long long>(n_total, 1);
     Ctl* ctl = (Ctl*)(base + L.ctl);
@@ -164,11 +192,11 @@ cudaError_t enqueue_batch(int G, long long n_total, int nnz, const long long* go
     if (e != cudaSuccess) return e;
     const int pb = 256;
     const int pgrid = (int)std::max<long long>(1, std::min<long long>((n_total + pb - 1) / pb, (long long)di.sms * 16));
-    // rows longer than kSmallRowMax entries number at most nnz / (kSmallRowMax + 1)
-    const int big_grid = (int)std::max<long long>(1, std::min<long long>(2LL * di.sms, nnz / (kSmallRowMax + 1)));
+    // rows longer than small_max entries number at most nnz / (small_max + 1)
+    const int big_grid = (int)std::max<long long>(1, std::min<long long>(2LL * di.sms, nnz / (t.small_max + 1)));
     if (G > 1) k_batch_validate<<<pgrid, pb, 0, s>>>(G, (int)n_total, goff, rowptr, colidx, ctl);
-    k_degree_validate<<<pgrid, pb, 0, s>>>((int)n_total, nnz, rowptr, colidx, deg, claim, vis, big, ctl, kSmallRowMax);
-    k_sort_rows_small<<<pgrid, pb, 0, s>>>((int)n_total, rowptr, colidx, deg, adj, ell, ctl);
+    k_degree_validate<<<pgrid, pb, 0, s>>>((int)n_total, nnz, rowptr, colidx, deg, claim, vis, big, ctl, t.small_max);
+    k_sort_rows_small<<<pgrid, pb, 0, s>>>((int)n_total, rowptr, colidx, deg, adj, ell, ctl, t.small_max);
     k_sort_rows_big<<<big_grid, 1024, sizeof(unsigned long long) * kBigRowSmem, s>>>(
         (int)n_total, rowptr, colidx, deg, adj, ell, big, ctl, (unsigned long long*)pool4);
     BatchArgs b;
@@ -193,12 +221,16 @@ cudaError_t enqueue_batch(int G, long long n_total, int nnz, const long long* go
     b.cc_gidx = (int*)(base + L.ccgi);
     b.cc_tab = (int4*)(base + L.cct);
     const int blocks = (int)std::min<long long>((long long)per_sm * di.sms, std::max(G, 1));
-    k_rcm_batch<kThreads><<<blocks, kThreads, 0, s>>>(b);
-    return cudaGetLastError();
+    void* kargs[] = {&b};
+    return cudaLaunchKernel(batch_kernel(t.threads), dim3(blocks), dim3(t.threads), kargs, 0, s);
 }
 
 rcm_status order_batch(int32_t G, int64_t n_total, const int64_t* goff, const int32_t* rowptr,
-                       const int32_t* colidx, int32_t* perm, cudaStream_t s) {
+                       const int32_t* colidx, int32_t* perm, const rcm_batch_options* opts, cudaStream_t s) {
+    BatchTuning t;
+    rcm_status st = batch_tuning(opts, &t);
+    if (st != RCM_OK) return st;
+    if (!batch_prepare(t)) return RCM_ERR_CUDA;
     // nnz is needed to size the sorted-adjacency copy: one 4-byte read, synchronised on s
     int nnz = 0;
     cudaError_t e = cudaMemcpyAsync(&nnz, rowptr + n_total, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -207,13 +239,118 @@ rcm_status order_batch(int32_t G, int64_t n_total, const int64_t* goff, const in
     if (nnz < 0) return RCM_ERR_BAD_CSR;
     const BatchLayout L = batch_layout(n_total, nnz);
     void* ws = nullptr;
-    rcm_status st = ws_alloc(&ws, L.total, s);
+    st = ws_alloc(&ws, L.total, s);
     if (st != RCM_OK) return st;
     char* base = (char*)ws;
-    e = enqueue_batch(G, n_total, nnz, (const long long*)goff, rowptr, colidx, perm, base, L, s);
+    e = enqueue_batch(G, n_total, nnz, (const long long*)goff, rowptr, colidx, perm, base, L, t, s);
     if (e == cudaSuccess) e = enqueue_latch((Ctl*)(base + L.ctl), stream_latch(s), nullptr, s);
     ws_free(ws, s);
     return e == cudaSuccess ? RCM_OK : cuda_status(e);
 }
 
+// Replay plan: the batched launches for fixed buffers, captured once into a CUDA graph.
+struct BatchPlan {
+    void* ws = nullptr;
+    Ctl* ctl = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+rcm_status batch_plan_create(int32_t G, int64_t n_total, int64_t nnz, const int64_t* goff, const int32_t* rowptr,
+                             const int32_t* colidx, int32_t* perm, const rcm_batch_options* opts, BatchPlan** out) {
+    BatchTuning t;
+    rcm_status st = batch_tuning(opts, &t);
+    if (st != RCM_OK) return st;
+    if (!batch_prepare(t)) return RCM_ERR_CUDA;
+    BatchPlan* p = new (std::nothrow) BatchPlan();
+    if (!p) return RCM_ERR_OOM;
+    const BatchLayout L = batch_layout(n_total, nnz);
+    cudaError_t e = cudaMalloc(&p->ws, L.total);
+    cudaStream_t cs = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        const cudaError_t ee = enqueue_batch(G, n_total, (int)nnz, (const long long*)goff, rowptr, colidx, perm,
+                                             (char*)p->ws, L, t, cs);
+        e = cudaStreamEndCapture(cs, &p->graph);
+        if (e == cudaSuccess) e = ee;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        if (p->exec) cudaGraphExecDestroy(p->exec);
+        if (p->graph) cudaGraphDestroy(p->graph);
+        if (p->ws) cudaFree(p->ws);
+        delete p;
+        return cuda_status(e);
+    }
+    p->ctl = (Ctl*)((char*)p->ws + L.ctl);
+    *out = p;
+    return RCM_OK;
+}
+
+rcm_status batch_plan_launch(BatchPlan* p, cudaStream_t s) {
+    const cudaError_t e = cudaGraphLaunch(p->exec, s);
+    return e == cudaSuccess ? RCM_OK : cuda_status(e);
+}
+
+rcm_status batch_plan_status(BatchPlan* p, cudaStream_t s) {
+    int bits = 0;
+    cudaError_t e = cudaMemcpyAsync(&bits, &p->ctl->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    return status_from_bits(bits);
+}
+
+void batch_plan_destroy(BatchPlan* p) {
+    cudaDeviceSynchronize();
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->ws) cudaFree(p->ws);
+    delete p;
+}
+
 }  // namespace rcm
+
+struct rcm_batch_plan {
+    rcm::BatchPlan* p;
+};
+
+extern "C" {
+
+rcm_status rcm_batch_plan_create(int32_t G, int64_t n_total, int64_t nnz, const int64_t* goff,
+                                 const int32_t* rowptr, const int32_t* colidx, int32_t* perm_out,
+                                 const rcm_batch_options* opts, rcm_batch_plan** out) {
+    if (!out || G <= 0 || n_total <= 0 || n_total >= 0x7fffffffLL || nnz < 0 || nnz >= 0x7fffffffLL)
+        return RCM_ERR_INVALID_ARG;
+    if (!goff || !rowptr || !perm_out || (nnz > 0 && !colidx)) return RCM_ERR_INVALID_ARG;
+    *out = nullptr;
+    rcm::BatchPlan* p = nullptr;
+    const rcm_status st = rcm::batch_plan_create(G, n_total, nnz, goff, rowptr, colidx, perm_out, opts, &p);
+    if (st != RCM_OK) return st;
+    *out = new (std::nothrow) rcm_batch_plan{p};
+    if (!*out) {
+        rcm::batch_plan_destroy(p);
+        return RCM_ERR_OOM;
+    }
+    return RCM_OK;
+}
+
+rcm_status rcm_batch_plan_launch(rcm_batch_plan* plan, rcm_stream_t stream) {
+    if (!plan) return RCM_ERR_INVALID_ARG;
+    return rcm::batch_plan_launch(plan->p, (cudaStream_t)stream);
+}
+
+rcm_status rcm_batch_plan_status(rcm_batch_plan* plan, rcm_stream_t stream) {
+    if (!plan) return RCM_ERR_INVALID_ARG;
+    return rcm::batch_plan_status(plan->p, (cudaStream_t)stream);
+}
+
+rcm_status rcm_batch_plan_destroy(rcm_batch_plan* plan) {
+    if (!plan) return RCM_ERR_INVALID_ARG;
+    rcm::batch_plan_destroy(plan->p);
+    delete plan;
+    return RCM_OK;
+}
+
+}  // extern "C"

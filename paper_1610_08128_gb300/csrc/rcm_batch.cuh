@@ -38,10 +38,23 @@ struct BatchLayout {
 };
 BatchLayout batch_layout(long long N, long long nnz);
 
+// Tuning of the batched path: CTA width of the executor (128, 256, 512) and the row length up to
+// which one thread sorts a row (4..kSmallRowMax). Every value gives the same result.
+struct BatchTuning {
+    int threads = 256;
+    int small_max = 32;
+};
+// RCM_OK and the tuning for the options, or RCM_ERR_INVALID_ARG.
+rcm_status batch_tuning(const rcm_batch_options* o, BatchTuning* out);
+
 // Enqueues on s, with the workspace at base (laid out by batch_layout(n_total, nnz)):
 // control-block reset, structural checks (block structure when G > 1; rowptr[n_total] == nnz),
 // degrees, sorted rows, then the batched engine. Device-detected errors land in the control block.
+// Call batch_prepare(t) first (outside any stream capture).
 cudaError_t enqueue_batch(int G, long long n_total, int nnz, const long long* goff, const int* rowptr,
-                          const int* colidx, int* perm, char* base, const BatchLayout& L, cudaStream_t s);
+                          const int* colidx, int* perm, char* base, const BatchLayout& L, const BatchTuning& t,
+                          cudaStream_t s);
+// One-time set-up of the kernels a tuning uses (attributes, occupancy); false on a CUDA error.
+bool batch_prepare(const BatchTuning& t);
 
 }  // namespace rcm

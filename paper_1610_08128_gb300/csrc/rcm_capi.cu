@@ -16,7 +16,7 @@ rcm_status order_single(int32_t n, int64_t nnz, const int32_t* rowptr, const int
                         int32_t* perm, const rcm_options* opts, long long* stats_dev, cudaEvent_t* ev,
                         cudaStream_t s);
 rcm_status order_batch(int32_t G, int64_t n_total, const int64_t* goff, const int32_t* rowptr,
-                       const int32_t* colidx, int32_t* perm, cudaStream_t s);
+                       const int32_t* colidx, int32_t* perm, const rcm_batch_options* opts, cudaStream_t s);
 
 rcm_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return RCM_OK;
@@ -268,7 +268,16 @@ rcm_status rcm_order_batch(int32_t G, int64_t n_total, const int64_t* goff, cons
     if (G < 0 || n_total < 0 || n_total >= 0x7fffffffLL) return RCM_ERR_INVALID_ARG;
     if (G == 0 || n_total == 0) return RCM_OK;
     if (!goff || !rowptr || !perm_out) return RCM_ERR_INVALID_ARG;
-    return order_batch(G, n_total, goff, rowptr, colidx, perm_out, (cudaStream_t)stream);
+    return order_batch(G, n_total, goff, rowptr, colidx, perm_out, nullptr, (cudaStream_t)stream);
+}
+
+rcm_status rcm_order_batch_ex(int32_t G, int64_t n_total, const int64_t* goff, const int32_t* rowptr,
+                              const int32_t* colidx, int32_t* perm_out, const rcm_batch_options* opts,
+                              rcm_stream_t stream) {
+    if (G < 0 || n_total < 0 || n_total >= 0x7fffffffLL) return RCM_ERR_INVALID_ARG;
+    if (G == 0 || n_total == 0) return RCM_OK;
+    if (!goff || !rowptr || !perm_out) return RCM_ERR_INVALID_ARG;
+    return order_batch(G, n_total, goff, rowptr, colidx, perm_out, opts, (cudaStream_t)stream);
 }
 
 rcm_status rcm_stream_status(rcm_stream_t stream) {

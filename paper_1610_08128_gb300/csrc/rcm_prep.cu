@@ -51,10 +51,10 @@ __global__ void k_degree_validate(int n, int nnz, const int* __restrict__ rowptr
 // Rows of at most kSmallRowMax stored entries: one thread per row (sort_small_row).
 __global__ void k_sort_rows_small(int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
                                   const int* __restrict__ deg, int* __restrict__ adj, int4* __restrict__ ell,
-                                  const Ctl* ctl) {
+                                  const Ctl* ctl, int small_max) {
     if (ctl->status & kErrBadCsr) return;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-        if (rowptr[v + 1] - rowptr[v] <= kSmallRowMax) sort_small_row(v, rowptr, colidx, deg, adj, ell);
+        if (rowptr[v + 1] - rowptr[v] <= small_max) sort_small_row(v, rowptr, colidx, deg, adj, ell);
 }
 
 // Rows longer than the per-thread sorter: one CTA per row, bitonic sort in shared memory for rows

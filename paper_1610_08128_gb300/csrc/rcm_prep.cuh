@@ -116,9 +116,11 @@ __global__ void k_degree_validate(int n, int nnz, const int* __restrict__ rowptr
                                   int* __restrict__ deg, unsigned long long* __restrict__ claim, int* __restrict__ vis,
                                   int* __restrict__ bigrows, Ctl* ctl, int small_max);
 
+// small_max (<= kSmallRowMax): rows with at most this many stored entries are sorted here, one
+// thread per row; k_degree_validate lists the longer ones for k_sort_rows_big with the same value.
 __global__ void k_sort_rows_small(int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
                                   const int* __restrict__ deg, int* __restrict__ adj, int4* __restrict__ ell,
-                                  const Ctl* ctl);
+                                  const Ctl* ctl, int small_max);
 
 __global__ void k_sort_rows_big(int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
                                 const int* __restrict__ deg, int* __restrict__ adj, int4* __restrict__ ell,

@@ -38,8 +38,11 @@
 
 namespace rcm {
 
-// Requests of at least this many vertices run on a cluster by default (see the header comment).
+// Requests of at least this many vertices run on a cluster of kServeClusterBlocks CTAs by default
+// (see the header comment). Small clusters measured best on GB300: they leave room on the SMs for
+// the single-CTA requests, while each large request keeps most of the speed of a wide grid.
 constexpr long long kServeClusterMin = 1LL << 18;
+constexpr int kServeClusterBlocks = 4;
 
 // Arena bytes of one request: the staged CSR and result when they are in host memory, a 256-byte
 // header holding the graph offsets {0, n} of a batch of one, and the larger of the two executors'
@@ -150,7 +153,7 @@ struct Server {
     int running = 0, max_running = 0;
     cudaError_t broken = cudaSuccess;  // first stream error seen: the context is unusable
     long long cluster_min = kServeClusterMin;  // -1: never
-    int cluster_blocks = 0;                    // 0: the largest cluster the device allows
+    int cluster_blocks = kServeClusterBlocks;
     bool trace = false;                // RCM_TRACE_ERRORS set: failed requests are reported on stderr
 };
 
@@ -227,7 +230,9 @@ static rcm_status launch_request(Server* s, Request* r) {
         hs->goff[0] = 0;
         hs->goff[1] = r->n;
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_goff, hs->goff, sizeof(hs->goff), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = enqueue_batch(1, r->n, (int)r->nnz, d_goff, rowptr, colidx, perm, ws, L, st);
+        const BatchTuning t;
+        if (!batch_prepare(t)) return RCM_ERR_CUDA;
+        if (e == cudaSuccess) e = enqueue_batch(1, r->n, (int)r->nnz, d_goff, rowptr, colidx, perm, ws, L, t, st);
         status_dev = (const int*)(ws + L.ctl + offsetof(Ctl, status));
     }
     if (e == cudaSuccess && r->out_host)
@@ -389,7 +394,7 @@ rcm_status rcm_server_create_ex(size_t hbm_budget_bytes, int32_t max_inflight, c
     s.max_inflight = max_inflight;
     if (opts) {
         s.cluster_min = opts->cluster_min_vertices == 0 ? kServeClusterMin : opts->cluster_min_vertices;
-        s.cluster_blocks = opts->cluster_blocks;
+        s.cluster_blocks = opts->cluster_blocks == 0 ? kServeClusterBlocks : opts->cluster_blocks;
     }
     s.slot_req.assign(max_inflight, nullptr);
     s.trace = std::getenv("RCM_TRACE_ERRORS") != nullptr;

@@ -132,7 +132,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_rcm_single(EngineArgs args, int
 // stamps and padded rows in shared memory (Engine<true, true>), so every level's row reads and
 // atomics stay inside one SM instead of going to L2.
 constexpr int kSmallMaxN = 4608;
-constexpr int kSmallThreads = 512;
 constexpr int kSmallSort = 256;  // component tables sorted in shared memory up to this size
 
 // Shared-memory layout: claims (8n bytes) at 0, stamps (4n) and then the padded rows (32n, read
@@ -142,7 +141,10 @@ static size_t small_vis_off(int n) { return align16(8 * (size_t)n); }
 static size_t small_ell_off(int n) { return align16(small_vis_off(n) + 4 * (size_t)n); }
 static size_t small_smem_bytes(int n) { return small_ell_off(n) + 32 * (size_t)n; }
 
-__global__ void __launch_bounds__(kSmallThreads, 1) k_rcm_small(EngineArgs args, int vis_off, int ell_off) {
+// kThreads: narrow graphs (a few dozen vertices per level) run best on small CTAs, whose barriers,
+// scans and reductions are cheap.
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads, 1) k_rcm_small(EngineArgs args, int vis_off, int ell_off) {
     extern __shared__ __align__(16) unsigned long long s_state[];
     __shared__ EngineSmem smem;
     __shared__ unsigned long long s_sort[kSmallSort + kSmallSort / 2];
@@ -152,7 +154,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_rcm_small(EngineArgs args,
     unsigned long long* claim = s_state;
     int* vis = (int*)((char*)s_state + vis_off);
     int4* ell = (int4*)((char*)s_state + ell_off);
-    for (int i = threadIdx.x; i < n; i += kSmallThreads) {
+    for (int i = threadIdx.x; i < n; i += kThreads) {
         claim[i] = kClaimNone;
         vis[i] = 0;
         ell[2 * i] = __ldg(args.ell + 2 * (size_t)i);
@@ -296,23 +298,42 @@ int single_cluster_max() {
 static std::once_flag g_small_once;
 static cudaError_t g_small_attr = cudaSuccess;
 
+static const void* small_kernel(int threads) {
+    switch (threads) {
+        case 32: return (const void*)k_rcm_small<32>;
+        case 64: return (const void*)k_rcm_small<64>;
+        case 128: return (const void*)k_rcm_small<128>;
+        case 256: return (const void*)k_rcm_small<256>;
+    }
+    return (const void*)k_rcm_small<512>;
+}
+
+// CTA width of the shared-memory executor when the caller does not choose one.
+// (256 was within a few percent of the best width on 2D and 3D grids and kNN meshes of 4,000
+// vertices on GB300; the best ranged from 128 on long 2D grids to 512 on many-component meshes.)
+static int small_default_threads(int) { return 256; }
+
 rcm_status single_launch(int n, const rcm_options& o, SingleLaunch* out) {
     const DeviceInfo& di = device_info();
     SingleLaunch sl;
     // the shared-memory CTA engine: on request, or automatically for small graphs when no option
     // shapes the persistent grid
-    const bool defaults = o.grid_blocks == 0 && o.cluster == 0 && o.narrow_threshold == 0 &&
-                          (o.block_threads == 0 || o.block_threads == kSmallThreads) && o.debug_stall_barrier == 0;
+    const bool defaults = o.grid_blocks == 0 && o.cluster == 0 && o.narrow_threshold == 0 && o.block_threads == 0 &&
+                          o.debug_stall_barrier == 0;
     if (o.executor == 2 || (o.executor == 0 && defaults && n <= kSmallMaxN)) {
         if (n > kSmallMaxN) return RCM_ERR_TOO_LARGE;
+        const int t = o.block_threads ? o.block_threads : small_default_threads(n);
+        if (t < 32 || t > 512) return RCM_ERR_INVALID_ARG;
         std::call_once(g_small_once, [] {
-            g_small_attr = cudaFuncSetAttribute(k_rcm_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)small_smem_bytes(kSmallMaxN));
+            for (int w : {32, 64, 128, 256, 512})
+                if (g_small_attr == cudaSuccess)
+                    g_small_attr = cudaFuncSetAttribute(small_kernel(w), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        (int)small_smem_bytes(kSmallMaxN));
         });
         if (g_small_attr != cudaSuccess) return RCM_ERR_CUDA;
-        single_blocks_per_sm(kSmallThreads);  // sets up the preprocessing kernels' attributes
+        single_blocks_per_sm(512);  // sets up the preprocessing kernels' attributes
         sl.small = true;
-        sl.threads = kSmallThreads;
+        sl.threads = t;
         sl.blocks = 1;
         sl.fused = o.fused_sweeps >= 0 ? 1 : 0;
         sl.profile = o.profile_phases ? 1 : 0;
@@ -373,7 +394,7 @@ cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* c
         const int pgrid = (int)std::min<long long>((n + pb - 1) / pb, (long long)di.sms * 16);
         k_degree_validate<<<std::max(pgrid, 1), pb, 0, s>>>(n, (int)nnz, rowptr, colidx, deg, claim, vis, bigrows, ctl,
                                                            kSmallRowMax);
-        k_sort_rows_small<<<std::max(pgrid, 1), pb, 0, s>>>(n, rowptr, colidx, deg, adj, ell, ctl);
+        k_sort_rows_small<<<std::max(pgrid, 1), pb, 0, s>>>(n, rowptr, colidx, deg, adj, ell, ctl, kSmallRowMax);
         // rows longer than kSmallRowMax entries number at most nnz / (kSmallRowMax + 1)
         const int big_grid = (int)std::max<long long>(1, std::min<long long>(2LL * di.sms, nnz / (kSmallRowMax + 1)));
         k_sort_rows_big<<<big_grid, 1024, sizeof(unsigned long long) * kBigRowSmem, s>>>(
@@ -421,8 +442,9 @@ cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* c
     int stall = sl.stall;
     void* kargs[] = {&args, &stall};
     if (sl.small) {
-        k_rcm_small<<<1, kSmallThreads, small_smem_bytes(n), s>>>(args, (int)small_vis_off(n), (int)small_ell_off(n));
-        e = cudaGetLastError();
+        int vo = (int)small_vis_off(n), eo = (int)small_ell_off(n);
+        void* sargs[] = {&args, &vo, &eo};
+        e = cudaLaunchKernel(small_kernel(sl.threads), dim3(1), dim3(sl.threads), sargs, small_smem_bytes(n), s);
     } else if (sl.cluster) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(sl.blocks);

@@ -43,6 +43,11 @@ class rcm_options(ctypes.Structure):
     ]
 
 
+class rcm_batch_options(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int32), ("row_sort_split", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
 class rcm_server_options(ctypes.Structure):
     _fields_ = [("cluster_min_vertices", ctypes.c_int64), ("cluster_blocks", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 5)]
@@ -93,6 +98,12 @@ def load():
         "rcm_order_host": ([I32, P, P, P, P], ctypes.c_int),
         "rcm_order_noalloc": ([I32, P, P, P, P], ctypes.c_int),
         "rcm_order_batch": ([I32, I64, P, P, P, P, P], ctypes.c_int),
+        "rcm_order_batch_ex": ([I32, I64, P, P, P, P, ctypes.POINTER(rcm_batch_options), P], ctypes.c_int),
+        "rcm_batch_plan_create": ([I32, I64, I64, P, P, P, P, ctypes.POINTER(rcm_batch_options),
+                                   ctypes.POINTER(P)], ctypes.c_int),
+        "rcm_batch_plan_launch": ([P, P], ctypes.c_int),
+        "rcm_batch_plan_status": ([P, P], ctypes.c_int),
+        "rcm_batch_plan_destroy": ([P], ctypes.c_int),
         "rcm_stream_status": ([P], ctypes.c_int),
         "rcm_workspace_bytes": ([I32, I64], SZ),
         "rcm_bandwidth_profile": ([I32, P, P, P, ctypes.POINTER(I64), ctypes.POINTER(I64), P], ctypes.c_int),
@@ -183,6 +194,38 @@ def rcm_order_batch(G, n_total, goff, rowptr, colidx, perm_out, stream=None) -> 
 
     return load().rcm_order_batch(int(G), int(n_total), _ptr(goff, True, torch.int64), _ptr(rowptr, True, _i32()),
                                   _ptr(colidx, True, _i32()), _ptr(perm_out, True, _i32()), _stream(stream))
+
+
+def rcm_order_batch_ex(G, n_total, goff, rowptr, colidx, perm_out, options=None, stream=None) -> int:
+    import torch
+
+    return load().rcm_order_batch_ex(int(G), int(n_total), _ptr(goff, True, torch.int64), _ptr(rowptr, True, _i32()),
+                                     _ptr(colidx, True, _i32()), _ptr(perm_out, True, _i32()),
+                                     ctypes.byref(options) if options is not None else None, _stream(stream))
+
+
+def rcm_batch_plan_create(G, n_total, nnz, goff, rowptr, colidx, perm_out, options=None):
+    """Returns (status, plan handle)."""
+    import torch
+
+    h = ctypes.c_void_p()
+    st = load().rcm_batch_plan_create(int(G), int(n_total), int(nnz), _ptr(goff, True, torch.int64),
+                                      _ptr(rowptr, True, _i32()), _ptr(colidx, True, _i32()),
+                                      _ptr(perm_out, True, _i32()),
+                                      ctypes.byref(options) if options is not None else None, ctypes.byref(h))
+    return st, h
+
+
+def rcm_batch_plan_launch(plan, stream=None) -> int:
+    return load().rcm_batch_plan_launch(plan, _stream(stream))
+
+
+def rcm_batch_plan_status(plan, stream=None) -> int:
+    return load().rcm_batch_plan_status(plan, _stream(stream))
+
+
+def rcm_batch_plan_destroy(plan) -> int:
+    return load().rcm_batch_plan_destroy(plan)
 
 
 def rcm_stream_status(stream=None) -> int:

@@ -330,3 +330,78 @@ def test_c2_grid192_full_size():
 def test_c3_mesh_full_size():
     g = synth.c3_mesh()
     assert_parity(g)
+
+
+def test_batch_options_and_replay_plan_match_oracle():
+    """Every batched tuning (CTA width, row-sort split) and a CUDA-graph replay plan return the
+    oracle's orders; the plan replays correctly after its inputs change."""
+    rcm = rcm_mod()
+    graphs = [synth.batch_graph(int(k), int(s), [78, i]) for i, (k, s) in
+              enumerate(zip(*synth.mix_sizes(40, 5, 3000, 78)[::-1]))]
+    graphs.append(synth.csr_from_edges(50, np.zeros(49, np.int64), np.arange(1, 50)))  # a 49-entry row
+    b = synth.concat(graphs)
+    goff = torch.from_numpy(b.goff).cuda()
+    rp = torch.from_numpy(b.rowptr).cuda()
+    ci = torch.from_numpy(b.colidx).cuda()
+    want = [oracle.rcm(g.n, g.rowptr, g.colidx) for g in graphs]
+
+    def check(perm):
+        host = perm.cpu().numpy()
+        for gi, g in enumerate(graphs):
+            assert np.array_equal(host[b.goff[gi]:b.goff[gi + 1]], want[gi]), gi
+
+    for threads in (128, 256, 512):
+        for split in (4, 8, 32):
+            o = rcm.rcm_batch_options()
+            o.block_threads, o.row_sort_split = threads, split
+            perm = torch.empty(b.n, dtype=torch.int32, device="cuda")
+            rcm.check(rcm.rcm_order_batch_ex(len(graphs), b.n, goff, rp, ci, perm, o), "batch_ex")
+            rcm.check(rcm.rcm_stream_status(), "batch_ex")
+            check(perm)
+    o = rcm.rcm_batch_options()
+    o.block_threads = 100
+    perm = torch.empty(b.n, dtype=torch.int32, device="cuda")
+    assert rcm.rcm_order_batch_ex(len(graphs), b.n, goff, rp, ci, perm, o) == rcm.RCM_ERR_INVALID_ARG
+
+    perm = torch.full((b.n,), -1, dtype=torch.int32, device="cuda")
+    st, plan = rcm.rcm_batch_plan_create(len(graphs), b.n, int(b.rowptr[-1]), goff, rp, ci, perm)
+    rcm.check(st, "plan")
+    try:
+        for _ in range(2):
+            rcm.check(rcm.rcm_batch_plan_launch(plan), "launch")
+            rcm.check(rcm.rcm_batch_plan_status(plan), "status")
+            check(perm)
+        # same structure, different ids inside each block: the replay orders the new pattern
+        graphs2 = [synth.permute(g, synth.rng_for([79, i]).permutation(g.n)) for i, g in enumerate(graphs)]
+        b2 = synth.concat(graphs2)
+        assert np.array_equal(b2.goff, b.goff) and b2.rowptr[-1] == b.rowptr[-1]
+        rp.copy_(torch.from_numpy(b2.rowptr))
+        ci.copy_(torch.from_numpy(b2.colidx))
+        rcm.check(rcm.rcm_batch_plan_launch(plan), "launch")
+        rcm.check(rcm.rcm_batch_plan_status(plan), "status")
+        host = perm.cpu().numpy()
+        for gi, g in enumerate(graphs2):
+            assert np.array_equal(host[b2.goff[gi]:b2.goff[gi + 1]], oracle.rcm(g.n, g.rowptr, g.colidx)), gi
+    finally:
+        rcm.check(rcm.rcm_batch_plan_destroy(plan), "destroy")
+
+
+def test_autotuner_picks_a_candidate_with_identical_results():
+    from paper_1610_08128_gb300 import tune
+
+    rcm = rcm_mod()
+    graphs = [synth.batch_graph(int(k), int(s), [80, i]) for i, (k, s) in
+              enumerate(zip(*synth.mix_sizes(30, 50, 2000, 80)[::-1]))]
+    b = synth.concat(graphs)
+    goff = torch.from_numpy(b.goff).cuda()
+    rp = torch.from_numpy(b.rowptr).cuda()
+    ci = torch.from_numpy(b.colidx).cuda()
+    perm = torch.empty(b.n, dtype=torch.int32, device="cuda")
+    best, table = tune.tune_batch(len(graphs), b.n, goff, rp, ci, perm, repeats=1)
+    assert best in tune.BATCH_CANDIDATES and len(table) == len(tune.BATCH_CANDIDATES)
+    g = synth.c1_grid2d()
+    rp1, ci1 = to_dev(g)
+    perm1 = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    best1, table1 = tune.tune_single(g.n, rp1, ci1, perm1, nnz=g.nnz, repeats=1)
+    assert best1 in tune.SINGLE_CANDIDATES and len(table1) == len(tune.SINGLE_CANDIDATES)
+    assert np.array_equal(perm1.cpu().numpy(), oracle.rcm(g.n, g.rowptr, g.colidx))
