@@ -369,8 +369,15 @@ def main():
     rp = torch.from_numpy(g.rowptr).cuda()
     ci = torch.from_numpy(g.colidx).cuda()
     perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    # launch shape picked by the autotuner on this graph (outside the timed region); every
+    # candidate returns the same permutation
+    from paper_1610_08128_gb300 import tune
+
+    tuned, _ = tune.tune_single(n, rp, ci, perm, nnz=nnz, repeats=3)
     opts = rcm.rcm_options()
     opts.nnz = nnz
+    for k, v in tuned.items():
+        setattr(opts, k, v)
     stream = torch.cuda.current_stream()
     l2 = torch.cuda.get_device_properties(local).L2_cache_size
     flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.int32, device="cuda")
@@ -467,7 +474,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": dict(cfg, parallelism="replicas" if world > 1 else "single",
+            "config": dict(cfg, parallelism="replicas" if world > 1 else "single", launch=tuned,
                            l2="inputs larger than L2, and a 2x-L2 buffer is written between steps"),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             # per step: k_degree_validate, k_sort_rows_small, k_sort_rows_big, k_rcm_single, k_latch

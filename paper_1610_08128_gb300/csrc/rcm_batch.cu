@@ -55,9 +55,10 @@ __global__ void __launch_bounds__(kThreads) k_rcm_batch(BatchArgs b) {
     while (true) {
         if (threadIdx.x == 0) s_item = atomicAdd(&b.ctl->work_next, 1);
         __syncthreads();
-        const int g = s_item;
+        const int item = s_item;
         __syncthreads();
-        if (g >= b.G) break;
+        if (item >= b.G) break;
+        const int g = b.order ? b.order[item] : item;
         const int v0 = (int)b.goff[g];
         const int n = (int)(b.goff[g + 1] - b.goff[g]);
         if (n == 0) continue;
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(kThreads) k_rcm_batch(BatchArgs b) {
     }
 }
 
-BatchLayout batch_layout(long long n_total, long long nnz) {
+BatchLayout batch_layout(long long n_total, long long nnz, long long G) {
     const size_t N = (size_t)std::max<long long>(n_total, 1), E = (size_t)std::max<long long>(nnz, 1);
     BatchLayout L;
     size_t o = 0;
@@ -126,8 +127,18 @@ BatchLayout batch_layout(long long n_total, long long nnz) {
     L.ccgk = take(sizeof(unsigned long long) * 2 * N);
     L.ccgi = take(sizeof(int) * 2 * N);
     L.cct = take(sizeof(int4) * N);
+    L.order = take(sizeof(int) * (size_t)std::max<long long>(G, 1));
     L.total = o;
     return L;
+}
+
+std::vector<int> batch_order(const std::vector<long long>& goff) {
+    const int G = (int)goff.size() - 1;
+    std::vector<int> order(std::max(G, 0));
+    for (int i = 0; i < G; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return goff[x + 1] - goff[x] > goff[y + 1] - goff[y]; });
+    return order;
 }
 
 static std::mutex g_batch_mu;
@@ -173,9 +184,9 @@ bool batch_prepare(const BatchTuning& t) {
     return batch_blocks_per_sm(t.threads) > 0;
 }
 
-cudaError_t enqueue_batch(int G, long long n_total, int nnz, const long long* goff, const int* rowptr,
-                          const int* colidx, int* perm, char* base, const BatchLayout& L, const BatchTuning& t,
-                          cudaStream_t s) {
+cudaError_t enqueue_batch(int G, long long n_total, int nnz, const long long* goff, const int* order,
+                          const int* rowptr, const int* colidx, int* perm, char* base, const BatchLayout& L,
+                          const BatchTuning& t, cudaStream_t s) {
     const DeviceInfo& di = device_info();
     const int per_sm = batch_blocks_per_sm(t.threads);
     if (per_sm <= 0) return cudaErrorInvalidConfiguration;
@@ -202,6 +213,7 @@ cudaError_t enqueue_batch(int G, long long n_total, int nnz, const long long* go
     BatchArgs b;
     b.G = G;
     b.goff = goff;
+    b.order = order;
     b.rowptr = rowptr;
     b.ell = ell;
     b.adj = adj;
@@ -231,18 +243,27 @@ rcm_status order_batch(int32_t G, int64_t n_total, const int64_t* goff, const in
     rcm_status st = batch_tuning(opts, &t);
     if (st != RCM_OK) return st;
     if (!batch_prepare(t)) return RCM_ERR_CUDA;
-    // nnz is needed to size the sorted-adjacency copy: one 4-byte read, synchronised on s
+    // nnz sizes the sorted-adjacency copy and the graph sizes set the work-queue order: one
+    // synchronised read of rowptr[n_total] and goff
     int nnz = 0;
+    std::vector<long long> goff_h((size_t)G + 1);
     cudaError_t e = cudaMemcpyAsync(&nnz, rowptr + n_total, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(goff_h.data(), goff, sizeof(long long) * goff_h.size(), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_status(e);
     if (nnz < 0) return RCM_ERR_BAD_CSR;
-    const BatchLayout L = batch_layout(n_total, nnz);
+    const BatchLayout L = batch_layout(n_total, nnz, G);
     void* ws = nullptr;
     st = ws_alloc(&ws, L.total, s);
     if (st != RCM_OK) return st;
     char* base = (char*)ws;
-    e = enqueue_batch(G, n_total, nnz, (const long long*)goff, rowptr, colidx, perm, base, L, t, s);
+    // pageable source: the copy returns once the data is staged, so the vector may go
+    const std::vector<int> order = batch_order(goff_h);
+    e = cudaMemcpyAsync(base + L.order, order.data(), sizeof(int) * (size_t)G, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = enqueue_batch(G, n_total, nnz, (const long long*)goff, (const int*)(base + L.order), rowptr, colidx,
+                          perm, base, L, t, s);
     if (e == cudaSuccess) e = enqueue_latch((Ctl*)(base + L.ctl), stream_latch(s), nullptr, s);
     ws_free(ws, s);
     return e == cudaSuccess ? RCM_OK : cuda_status(e);
@@ -264,13 +285,21 @@ rcm_status batch_plan_create(int32_t G, int64_t n_total, int64_t nnz, const int6
     if (!batch_prepare(t)) return RCM_ERR_CUDA;
     BatchPlan* p = new (std::nothrow) BatchPlan();
     if (!p) return RCM_ERR_OOM;
-    const BatchLayout L = batch_layout(n_total, nnz);
+    const BatchLayout L = batch_layout(n_total, nnz, G);
     cudaError_t e = cudaMalloc(&p->ws, L.total);
+    // work-queue order (largest graph first) from the graph offsets at creation
+    std::vector<long long> goff_h((size_t)G + 1);
+    if (e == cudaSuccess) e = cudaMemcpy(goff_h.data(), goff, sizeof(long long) * goff_h.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) {
+        const std::vector<int> order = batch_order(goff_h);
+        e = cudaMemcpy((char*)p->ws + L.order, order.data(), sizeof(int) * (size_t)G, cudaMemcpyHostToDevice);
+    }
     cudaStream_t cs = nullptr;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        const cudaError_t ee = enqueue_batch(G, n_total, (int)nnz, (const long long*)goff, rowptr, colidx, perm,
+        const cudaError_t ee = enqueue_batch(G, n_total, (int)nnz, (const long long*)goff,
+                                             (const int*)((char*)p->ws + L.order), rowptr, colidx, perm,
                                              (char*)p->ws, L, t, cs);
         e = cudaStreamEndCapture(cs, &p->graph);
         if (e == cudaSuccess) e = ee;

@@ -2,6 +2,8 @@
 // shared by rcm_order_batch and the serving path (which runs each request as a batch of one).
 #pragma once
 
+#include <vector>
+
 #include "rcm_internal.cuh"
 
 namespace rcm {
@@ -9,6 +11,7 @@ namespace rcm {
 struct BatchArgs {
     int G;
     const long long* goff;
+    const int* order;  // graph of each work-queue position (largest first); null = index order
     // component tables: per-vertex arrays indexed by global id; per-graph lists at v0 (2 v0 for
     // the sort scratch)
     int* cc_parent;
@@ -34,9 +37,12 @@ struct BatchArgs {
 // Byte offsets of the workspace of N vertices (all graphs together) and nnz stored entries, each
 // 256-byte aligned; total = bytes to allocate.
 struct BatchLayout {
-    size_t ctl, pool, deg, claim, vis, big, adj, ell, ccs, cck, ccr, ccgk, ccgi, cct, total;
+    size_t ctl, pool, deg, claim, vis, big, adj, ell, ccs, cck, ccr, ccgk, ccgi, cct, order, total;
 };
-BatchLayout batch_layout(long long N, long long nnz);
+BatchLayout batch_layout(long long N, long long nnz, long long G = 1);
+
+// Work-queue order of G graphs: largest first (ties by index), from the host copy of goff.
+std::vector<int> batch_order(const std::vector<long long>& goff);
 
 // Tuning of the batched path: CTA width of the executor (128, 256, 512) and the row length up to
 // which one thread sorts a row (4..kSmallRowMax). Every value gives the same result.
@@ -51,9 +57,10 @@ rcm_status batch_tuning(const rcm_batch_options* o, BatchTuning* out);
 // control-block reset, structural checks (block structure when G > 1; rowptr[n_total] == nnz),
 // degrees, sorted rows, then the batched engine. Device-detected errors land in the control block.
 // Call batch_prepare(t) first (outside any stream capture).
-cudaError_t enqueue_batch(int G, long long n_total, int nnz, const long long* goff, const int* rowptr,
-                          const int* colidx, int* perm, char* base, const BatchLayout& L, const BatchTuning& t,
-                          cudaStream_t s);
+// order: device, the work-queue order (G ints), or null for index order.
+cudaError_t enqueue_batch(int G, long long n_total, int nnz, const long long* goff, const int* order,
+                          const int* rowptr, const int* colidx, int* perm, char* base, const BatchLayout& L,
+                          const BatchTuning& t, cudaStream_t s);
 // One-time set-up of the kernels a tuning uses (attributes, occupancy); false on a CUDA error.
 bool batch_prepare(const BatchTuning& t);
 

@@ -232,7 +232,7 @@ static rcm_status launch_request(Server* s, Request* r) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_goff, hs->goff, sizeof(hs->goff), cudaMemcpyHostToDevice, st);
         const BatchTuning t;
         if (!batch_prepare(t)) return RCM_ERR_CUDA;
-        if (e == cudaSuccess) e = enqueue_batch(1, r->n, (int)r->nnz, d_goff, rowptr, colidx, perm, ws, L, t, st);
+        if (e == cudaSuccess) e = enqueue_batch(1, r->n, (int)r->nnz, d_goff, nullptr, rowptr, colidx, perm, ws, L, t, st);
         status_dev = (const int*)(ws + L.ctl + offsetof(Ctl, status));
     }
     if (e == cudaSuccess && r->out_host)

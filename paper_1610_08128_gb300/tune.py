@@ -21,7 +21,9 @@ BATCH_CANDIDATES = [
 
 SINGLE_CANDIDATES = [
     {"executor": 1},
+    {"executor": 1, "narrow_threshold": 128},
     {"executor": 1, "narrow_threshold": 256},
+    {"executor": 1, "narrow_threshold": 512},
     {"executor": 1, "narrow_threshold": 2048},
     {"executor": 2, "block_threads": 128},
     {"executor": 2, "block_threads": 256},

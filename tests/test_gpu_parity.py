@@ -321,9 +321,43 @@ def test_batch_rejects_cross_block_entries():
 
 @pytest.mark.slow
 def test_c2_grid192_full_size():
-    """The full 192^3 workload, in the launch configuration the benchmark times."""
+    """The full 192^3 workload, in the launch configurations the benchmark's tuner chooses from
+    (frontier-switch thresholds of the persistent grid)."""
     g = synth.c2_grid3d()
-    assert_parity(g)
+    want = oracle.rcm(g.n, g.rowptr, g.colidx)
+    for opts in [None, {"narrow_threshold": 128}, {"narrow_threshold": 256}, {"narrow_threshold": 512}]:
+        assert np.array_equal(gpu_perm(g, opts), want), opts
+
+
+@pytest.mark.slow
+def test_c4_batch_full_size_sampled():
+    """The full 10,000-graph batch, ordered as the benchmark does (tuned options, replay plan);
+    a sample of graphs, including the largest, is checked against the oracle one by one."""
+    from paper_1610_08128_gb300 import tune
+
+    rcm = rcm_mod()
+    b = synth.c4_batch(workers=synth.default_workers())
+    goff = torch.from_numpy(b.goff).cuda()
+    rp = torch.from_numpy(b.rowptr).cuda()
+    ci = torch.from_numpy(b.colidx).cuda()
+    perm = torch.empty(b.n, dtype=torch.int32, device="cuda")
+    best, _ = tune.tune_batch(b.G, b.n, goff, rp, ci, perm, repeats=1)
+    o = rcm.rcm_batch_options()
+    for k, v in best.items():
+        setattr(o, k, v)
+    st, plan = rcm.rcm_batch_plan_create(b.G, b.n, int(b.rowptr[-1]), goff, rp, ci, perm, o)
+    rcm.check(st, "plan")
+    try:
+        rcm.check(rcm.rcm_batch_plan_launch(plan), "launch")
+        rcm.check(rcm.rcm_batch_plan_status(plan), "status")
+    finally:
+        rcm.rcm_batch_plan_destroy(plan)
+    host = perm.cpu().numpy()
+    sizes = np.diff(b.goff)
+    sample = list(synth.rng_for(81).choice(b.G, 60, replace=False)) + [int(np.argmax(sizes))]
+    for gi in sample:
+        g = b.graphs[gi]
+        assert np.array_equal(host[b.goff[gi]:b.goff[gi + 1]], oracle.rcm(g.n, g.rowptr, g.colidx)), gi
 
 
 @pytest.mark.slow
