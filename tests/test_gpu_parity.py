@@ -439,3 +439,27 @@ def test_autotuner_picks_a_candidate_with_identical_results():
     best1, table1 = tune.tune_single(g.n, rp1, ci1, perm1, nnz=g.nnz, repeats=1)
     assert best1 in tune.SINGLE_CANDIDATES and len(table1) == len(tune.SINGLE_CANDIDATES)
     assert np.array_equal(perm1.cpu().numpy(), oracle.rcm(g.n, g.rowptr, g.colidx))
+
+
+def test_quality_report_permutes_the_matrix():
+    """P A P^T built on the device equals the host permutation; SpMV on it equals the permuted
+    product; the report's bandwidth and profile equal the oracle's."""
+    from paper_1610_08128_gb300 import quality
+
+    g = synth.c3_mesh(20000)
+    want = oracle.rcm(g.n, g.rowptr, g.colidx)
+    rp, ci = to_dev(g)
+    perm = torch.from_numpy(np.asarray(want, dtype=np.int32)).cuda()
+    prp, pci = quality.permute_csr(rp, ci, perm)
+    pos = np.empty(g.n, np.int64)
+    pos[want] = np.arange(g.n)
+    h = synth.permute(g, pos)
+    assert np.array_equal(prp.cpu().numpy(), h.rowptr) and np.array_equal(pci.cpu().numpy(), h.colidx)
+    vals = torch.ones(ci.numel(), dtype=torch.float32, device="cuda")
+    a = torch.sparse_csr_tensor(rp, ci, vals, size=(g.n, g.n))
+    b = torch.sparse_csr_tensor(prp, pci, vals, size=(g.n, g.n))
+    x = torch.rand(g.n, 1, device="cuda")
+    assert torch.allclose((a @ x)[perm.long()], b @ x[perm.long()], rtol=1e-5, atol=1e-5)
+    r = quality.report(rp, ci, perm, repeats=2)
+    assert (r["bandwidth_rcm"], r["profile_rcm"]) == oracle.bandwidth_profile(g.n, g.rowptr, g.colidx, want)
+    assert r["bandwidth_rcm"] < r["bandwidth_original"]
