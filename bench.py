@@ -70,10 +70,15 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+# the sources that define the persistent traversal kernel (k_rcm_single) and its launch
+TRAVERSAL_SOURCES = ["rcm_single.cu", "rcm_single.cuh", "rcm_engine.cuh", "rcm_internal.cuh", "rcm_cc.cuh",
+                     "rcm_prep.cuh", "rcm_host.hpp"]
+
+
 def kernel_sources_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1610_08128_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in TRAVERSAL_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())

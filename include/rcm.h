@@ -251,7 +251,10 @@ typedef struct {
                                      engine of rcm_order launched as one thread-block cluster;
                                      smaller ones run on one CTA. 0 = 262,144; -1 = never         */
     int32_t cluster_blocks;       /* CTAs of that cluster, 2..16 as the device allows; 0 = 4       */
-    int32_t reserved[5];
+    int32_t debug_fail_after;     /* test hook: once this many requests have completed, the server
+                                     acts as if a running request's stream reported a CUDA error
+                                     (its failure path without a device fault); 0 = off           */
+    int32_t reserved[4];
 } rcm_server_options;
 
 /* rcm_server_create with an execution policy (opts may be NULL). RCM_ERR_INVALID_ARG for values
@@ -261,9 +264,10 @@ rcm_status rcm_server_create_ex(size_t hbm_budget_bytes, int32_t max_inflight, c
 
 /*
  * Submits one ordering request and returns its ticket. rowptr/colidx may be host or device
- * memory, perm_out host or device memory (pinned host memory gives the fastest copies); all must
- * stay valid and unmodified until rcm_poll/rcm_wait reports the request finished. A request
- * that can never fit the budget returns RCM_ERR_TOO_LARGE (no ticket).
+ * memory, perm_out host or device memory (pinned host memory gives the fastest copies; results
+ * bound for pageable memory are copied by a helper thread of the server once the ordering is
+ * done); all must stay valid and unmodified until rcm_poll/rcm_wait reports the request
+ * finished. A request that can never fit the budget returns RCM_ERR_TOO_LARGE (no ticket).
  */
 rcm_status rcm_submit(rcm_server *srv, int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *colidx,
                       int32_t *perm_out, uint64_t *ticket);

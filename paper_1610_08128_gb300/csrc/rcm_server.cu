@@ -122,6 +122,8 @@ struct Request {
     const int* colidx;
     int* perm;
     bool in_host, out_host;
+    bool out_pageable = false;   // result copied to pageable memory by the copier thread
+    int* staged_perm = nullptr;  // the result inside the request's region (host outputs)
     size_t off = 0, bytes = 0;
     int slot = -1;
     int state = 0;  // 0 waiting, 1 running, 2 done
@@ -147,6 +149,13 @@ struct Server {
     std::unordered_map<uint64_t, Request*> reqs;
     std::vector<double> latencies;
     std::thread worker;
+    // results bound for pageable host memory: copied by this thread (a synchronous copy would
+    // stall the worker), which then completes the request
+    std::thread copier;
+    std::deque<Request*> to_copy;
+    std::condition_variable ccv;
+    bool copier_stop = false;
+    cudaStream_t copy_stream = nullptr;
     bool stop = false;
     uint64_t next_ticket = 1;
     long long submitted = 0, completed = 0, failed = 0, cancelled = 0;
@@ -154,6 +163,7 @@ struct Server {
     cudaError_t broken = cudaSuccess;  // first stream error seen: the context is unusable
     long long cluster_min = kServeClusterMin;  // -1: never
     int cluster_blocks = kServeClusterBlocks;
+    int debug_fail_after = 0;                  // test hook (rcm_server_options)
     bool trace = false;                // RCM_TRACE_ERRORS set: failed requests are reported on stderr
 };
 
@@ -162,6 +172,20 @@ struct alignas(64) SlotHost {
     long long goff[2];
     int status;
 };
+
+// Marks a running request done and frees its region and slot (caller holds the lock).
+static void complete_locked(Server* s, Request* r) {
+    s->slot_req[r->slot] = nullptr;
+    r->t_done = now_s();
+    r->state = 2;
+    s->alloc.release(r->off, r->bytes);
+    s->free_slots.push_back(r->slot);
+    s->running--;
+    s->completed++;
+    if (r->status != RCM_OK) s->failed++;
+    s->latencies.push_back(r->t_done - r->t_submit);
+    s->cv.notify_all();
+}
 
 static void CUDART_CB on_request_done(void* p) {
     Request* r = (Request*)p;
@@ -173,16 +197,32 @@ static void CUDART_CB on_request_done(void* p) {
     if (s->trace && r->status != RCM_OK)
         std::fprintf(stderr, "rcm server: request %llu (n=%d, nnz=%lld) failed with device status bits %d\n",
                      (unsigned long long)r->ticket, r->n, r->nnz, bits);
-    s->slot_req[r->slot] = nullptr;
-    r->t_done = now_s();
-    r->state = 2;
-    s->alloc.release(r->off, r->bytes);
-    s->free_slots.push_back(r->slot);
-    s->running--;
-    s->completed++;
-    if (r->status != RCM_OK) s->failed++;
-    s->latencies.push_back(r->t_done - r->t_submit);
-    s->cv.notify_all();
+    if (r->out_pageable && r->status == RCM_OK) {
+        s->to_copy.push_back(r);  // the copier moves the result, then completes the request
+        s->ccv.notify_one();
+        return;
+    }
+    complete_locked(s, r);
+}
+
+static void copier_loop(Server* s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        s->ccv.wait(lk, [&] { return !s->to_copy.empty() || s->copier_stop; });
+        if (s->to_copy.empty()) break;  // stopping, nothing left
+        Request* r = s->to_copy.front();
+        s->to_copy.pop_front();
+        if (r->state == 2) continue;  // finished by the failure path meanwhile
+        lk.unlock();
+        cudaError_t e = cudaMemcpyAsync(r->perm, r->staged_perm, sizeof(int) * (size_t)r->n, cudaMemcpyDeviceToHost,
+                                        s->copy_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy_stream);
+        lk.lock();
+        if (r->state == 2) continue;
+        if (e != cudaSuccess) r->status = cuda_status(e);
+        complete_locked(s, r);
+    }
 }
 
 // Enqueue the work of an admitted request on its slot's stream (caller holds no lock).
@@ -235,7 +275,8 @@ static rcm_status launch_request(Server* s, Request* r) {
         if (e == cudaSuccess) e = enqueue_batch(1, r->n, (int)r->nnz, d_goff, nullptr, rowptr, colidx, perm, ws, L, t, st);
         status_dev = (const int*)(ws + L.ctl + offsetof(Ctl, status));
     }
-    if (e == cudaSuccess && r->out_host)
+    r->staged_perm = perm;
+    if (e == cudaSuccess && r->out_host && !r->out_pageable)
         e = cudaMemcpyAsync(r->perm, perm, sizeof(int) * (size_t)r->n, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hs->status, status_dev, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaLaunchHostFunc(st, on_request_done, r);
@@ -341,6 +382,9 @@ static void worker_loop(Server* s) {
         if (s->running > 0 && s->broken == cudaSuccess) {
             s->cv.wait_for(lk, std::chrono::milliseconds(20));
             check_streams(s, lk);
+            if (s->debug_fail_after > 0 && s->completed >= s->debug_fail_after && s->running > 0 &&
+                s->broken == cudaSuccess)
+                fail_all(s, cudaErrorLaunchFailure);
         } else {
             s->cv.wait(lk);
         }
@@ -371,7 +415,7 @@ rcm_status rcm_server_create_ex(size_t hbm_budget_bytes, int32_t max_inflight, c
     if (!out || hbm_budget_bytes == 0 || max_inflight <= 0 || max_inflight > 4096) return RCM_ERR_INVALID_ARG;
     *out = nullptr;
     if (opts && (opts->cluster_min_vertices < -1 || opts->cluster_blocks < 0 || opts->cluster_blocks > 16 ||
-                 opts->cluster_blocks == 1))
+                 opts->cluster_blocks == 1 || opts->debug_fail_after < 0))
         return RCM_ERR_INVALID_ARG;
     rcm_server* srv = new (std::nothrow) rcm_server();
     if (!srv) return RCM_ERR_OOM;
@@ -395,6 +439,7 @@ rcm_status rcm_server_create_ex(size_t hbm_budget_bytes, int32_t max_inflight, c
     if (opts) {
         s.cluster_min = opts->cluster_min_vertices == 0 ? kServeClusterMin : opts->cluster_min_vertices;
         s.cluster_blocks = opts->cluster_blocks == 0 ? kServeClusterBlocks : opts->cluster_blocks;
+        s.debug_fail_after = opts->debug_fail_after;
     }
     s.slot_req.assign(max_inflight, nullptr);
     s.trace = std::getenv("RCM_TRACE_ERRORS") != nullptr;
@@ -411,7 +456,17 @@ rcm_status rcm_server_create_ex(size_t hbm_budget_bytes, int32_t max_inflight, c
         delete srv;
         return cuda_status(e);
     }
+    e = cudaStreamCreateWithFlags(&s.copy_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        for (cudaStream_t st : s.streams)
+            if (st) cudaStreamDestroy(st);
+        cudaFreeHost(s.h_slots);
+        cudaFree(s.arena);
+        delete srv;
+        return cuda_status(e);
+    }
     s.worker = std::thread(worker_loop, &s);
+    s.copier = std::thread(copier_loop, &s);
     *out = srv;
     return RCM_OK;
 }
@@ -438,6 +493,15 @@ rcm_status rcm_submit(rcm_server* srv, int32_t n, int64_t nnz, const int32_t* ro
     r->perm = perm_out;
     r->in_host = !is_device(rowptr);
     r->out_host = !is_device(perm_out);
+    if (r->out_host) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, perm_out) != cudaSuccess) {
+            cudaGetLastError();
+            r->out_pageable = true;
+        } else {
+            r->out_pageable = at.type != cudaMemoryTypeHost;
+        }
+    }
     r->bytes = request_bytes(n, nnz, r->in_host, r->out_host);
     r->srv = &s;
     r->t_submit = now_s();
@@ -555,7 +619,14 @@ rcm_status rcm_server_destroy(rcm_server* srv) {
         s.stop = true;
         s.cv.notify_all();
     }
-    if (s.worker.joinable()) s.worker.join();
+    if (s.worker.joinable()) s.worker.join();  // returns once no request is running or waiting
+    {
+        std::lock_guard<std::mutex> g(s.mu);
+        s.copier_stop = true;
+        s.ccv.notify_all();
+    }
+    if (s.copier.joinable()) s.copier.join();
+    if (s.copy_stream) cudaStreamDestroy(s.copy_stream);
     for (cudaStream_t st : s.streams) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);

@@ -50,7 +50,7 @@ class rcm_batch_options(ctypes.Structure):
 
 class rcm_server_options(ctypes.Structure):
     _fields_ = [("cluster_min_vertices", ctypes.c_int64), ("cluster_blocks", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("debug_fail_after", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class rcm_stats(ctypes.Structure):

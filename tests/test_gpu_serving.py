@@ -158,6 +158,40 @@ def test_cancel_and_failed_requests(rcm):
         rcm.rcm_server_destroy(srv)
 
 
+def test_stream_error_fails_outstanding_requests(rcm):
+    """Failure handling without a device fault: a test hook makes the worker act as if a running
+    request's stream reported an error once two requests have completed. Every outstanding request
+    then finishes with RCM_ERR_CUDA (no waiter blocks), completed ones keep their correct results,
+    later submissions are refused, and destroy returns."""
+    graphs = [synth.grid((400, 400), seed=20 + i) for i in range(16)]
+    o = rcm.rcm_server_options()
+    o.debug_fail_after = 2
+    st, srv = rcm.rcm_server_create_ex(4 << 30, 2, o)
+    rcm.check(st, "create")
+    try:
+        outs, tickets = [], []
+        for g in graphs:
+            out = torch.empty(g.n, dtype=torch.int32)
+            s, t = rcm.rcm_submit(srv, g.n, g.nnz, torch.from_numpy(g.rowptr), torch.from_numpy(g.colidx), out)
+            rcm.check(s, "submit")
+            outs.append(out)
+            tickets.append(t)
+        statuses = [rcm.rcm_wait(srv, t) for t in tickets]
+        assert set(statuses) <= {rcm.RCM_OK, rcm.RCM_ERR_CUDA}
+        assert statuses.count(rcm.RCM_OK) >= 2 and rcm.RCM_ERR_CUDA in statuses
+        for g, s_, out in zip(graphs, statuses, outs):
+            if s_ == rcm.RCM_OK:
+                assert np.array_equal(out.numpy(), oracle.rcm(g.n, g.rowptr, g.colidx))
+        g = graphs[0]
+        s, _ = rcm.rcm_submit(srv, g.n, g.nnz, torch.from_numpy(g.rowptr), torch.from_numpy(g.colidx),
+                              torch.empty(g.n, dtype=torch.int32))
+        assert s == rcm.RCM_ERR_CUDA
+        _, info = rcm.rcm_server_info(srv)
+        assert info["failed"] == statuses.count(rcm.RCM_ERR_CUDA)
+    finally:
+        assert rcm.rcm_server_destroy(srv) == rcm.RCM_OK
+
+
 def test_destroy_with_waiting_requests(rcm):
     g = synth.grid((120, 120), seed=4)
     st, srv = rcm.rcm_server_create(region_bytes(g), 1)
