@@ -54,6 +54,12 @@ def test_host_only_functions(lib):
     # staging the output adds its 4n bytes (4 * 4096 is already a multiple of the 256-byte alignment)
     assert rcm.rcm_request_bytes(4096, 16128, False, True) == rcm.rcm_request_bytes(4096, 16128, False, False) + 4 * 4096
     assert rcm.rcm_request_bytes(-1, 0) == 0
+    # sizes at the int32 limits: plain arithmetic, no overflow, monotone in n and nnz
+    big = rcm.rcm_workspace_bytes(2**31 - 1, 2**31 - 2)
+    assert big > 80 * (2**31 - 1) + 4 * (2**31 - 2) and big < 2**45
+    assert rcm.rcm_workspace_bytes(2**31 - 1, 0) < big
+    rb = rcm.rcm_request_bytes(2**31 - 1, 2**31 - 2, True, True)
+    assert rb > big and rb < 2**46
 
 
 def test_binding_refuses_missing_library(monkeypatch, tmp_path):
