@@ -49,6 +49,9 @@ def parse_args():
     p.add_argument("--serve-requests", type=int, default=4000)
     p.add_argument("--serve-pool", type=int, default=256)
     p.add_argument("--serve-rate", type=float, default=2000.0)
+    p.add_argument("--launch", default=None,
+                   help="options of the one-graph engine, skipping the autotuner: key=value pairs such as "
+                        "executor=1,narrow_threshold=512 (or a JSON object)")
     return p.parse_args()
 
 
@@ -71,8 +74,8 @@ def load_peaks():
 
 
 # the sources that define the persistent traversal kernel (k_rcm_single) and its launch
-TRAVERSAL_SOURCES = ["rcm_single.cu", "rcm_single.cuh", "rcm_engine.cuh", "rcm_internal.cuh", "rcm_cc.cuh",
-                     "rcm_prep.cuh", "rcm_host.hpp"]
+TRAVERSAL_SOURCES = ["rcm_single.cu", "rcm_single.cuh", "rcm_single_kernels.cuh", "rcm_kern_grid512.cu",
+                     "rcm_engine.cuh", "rcm_internal.cuh", "rcm_cc.cuh", "rcm_prep.cuh", "rcm_host.hpp"]
 
 
 def kernel_sources_hash() -> str:
@@ -83,6 +86,18 @@ def kernel_sources_hash() -> str:
             h.update(f.encode())
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def parse_launch(text: str) -> dict:
+    """Engine options from "k=v,k=v" (integers) or a JSON object."""
+    text = text.strip()
+    if text.startswith("{"):
+        return {k: int(v) for k, v in json.loads(text).items()}
+    out = {}
+    for part in filter(None, text.split(",")):
+        k, v = part.split("=")
+        out[k.strip()] = int(v)
+    return out
 
 
 def recorded_traffic(kernel: str, workload: str):
@@ -379,7 +394,10 @@ def main():
     # candidate returns the same permutation
     from paper_1610_08128_gb300 import tune
 
-    tuned, _ = tune.tune_single(n, rp, ci, perm, nnz=nnz, repeats=3)
+    if args.launch:
+        tuned = parse_launch(args.launch)
+    else:
+        tuned, _ = tune.tune_single(n, rp, ci, perm, nnz=nnz, repeats=3)
     opts = rcm.rcm_options()
     opts.nnz = nnz
     for k, v in tuned.items():

@@ -89,6 +89,15 @@ typedef struct {
                                   1 = always the persistent grid. 2 = always the shared-memory CTA
                                   (RCM_ERR_TOO_LARGE above 4,608 vertices); with 2, block_threads
                                   (32..512, 0 = automatic) sets that CTA's width                     */
+    int32_t async_sweeps;      /* levels-only sweeps of the persistent grid (Alg. 2 needs only their
+                                  eccentricity and last level): 1 = through an asynchronous work queue
+                                  with no grid barrier per level (same result; 8n more workspace
+                                  bytes; block_threads must be 0 or 512, else RCM_ERR_INVALID_ARG);
+                                  0 or -1 = level by level (the default: faster on every graph
+                                  measured on GB300). The shared-memory CTA ignores it.             */
+    int32_t debug_async_slots; /* test hook: slots of the asynchronous sweeps' work queue (0 = 2n).
+                                  A queue that runs full makes the sweep, and every later one of
+                                  the call, run level by level instead: same result, slower.        */
 } rcm_options;
 
 /* Statistics of one ordering (filled by rcm_order_ex when requested). */

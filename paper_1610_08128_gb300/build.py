@@ -15,9 +15,13 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ_DIR = os.path.join(HERE, "_build")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "librcm_gb300.so")
-SOURCES = ["rcm_capi.cu", "rcm_prep.cu", "rcm_single.cu", "rcm_batch.cu", "rcm_server.cu"]
+SOURCES = [*(f"rcm_kern_grid{w}.cu" for w in (32, 64, 128, 256, 512, 1024)), "rcm_kern_grid512_async.cu",
+           "rcm_kern_small.cu",
+           "rcm_batch.cu", "rcm_capi.cu", "rcm_prep.cu", "rcm_single.cu", "rcm_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xcompiler", "-Wall"]
+# Kernel templates are instantiated once, in their own translation units, and launched from the
+# host code of another: their host stubs need ordinary (not file-static) linkage.
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-static-global-template-stub=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xcompiler", "-Wall"]
 
 
 def nvcc() -> str:

@@ -83,6 +83,11 @@ struct EngineArgs {
     int4* cc_tab;                // cc_cap entries: (start vertex, first label, size, root)
     int cc_cap;                  // most components ordered concurrently (else one by one)
     int cc_big;                  // components at least this large run on the whole grid
+    // asynchronous levels-only sweeps (whole-grid executor only; adist == null: level by level)
+    unsigned long long* adist;   // n words: (~sweep stamp) << 32 | breadth-first distance
+    unsigned long long* aq;      // work queue of aq_cap (distance << 32 | vertex) items
+    AsyncCtl* actl;
+    unsigned aq_cap;
 };
 
 enum { kPhExpand = 0, kPhClaim, kPhOwn, kPhLabels, kPhExchange, kPhRedist, kPhWaitNarrow, kPhOther };
@@ -101,6 +106,7 @@ struct EngineSmem {
     int bc[8];
     unsigned long long bck;
     int tail;
+    int aflag;                   // async sweep: stop flag relayed to the CTA's warps
     int cache[2][kCache];
 };
 
@@ -120,13 +126,18 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
 // kSmem (CTA engines only): the claims, visit stamps and padded rows of the graph live in shared
 // memory, indexed from the graph's first vertex v0; otherwise they are global arrays indexed by
 // vertex id.
-template <bool kCtaOnly, bool kSmem = false>
+// kAsync (whole-grid engine only): levels-only sweeps through the asynchronous work queue when
+// the arguments provide it. A separate instantiation, so the level-by-level kernels carry none of
+// its code or registers.
+template <bool kCtaOnly, bool kSmem = false, bool kAsync = false>
 struct Engine {
     static_assert(kCtaOnly || !kSmem, "shared-memory state needs a CTA engine");
+    static_assert(!kAsync || !kCtaOnly, "asynchronous sweeps need the whole grid");
     const EngineArgs* a;   // in shared memory (keeps the per-thread register footprint small)
     unsigned epoch;
     int sweep_id;
     int scan_par;          // alternates between consecutive CTA scans (see block_excl_scan)
+    bool async_ok;         // asynchronous levels-only sweeps still enabled (off once the queue ran full)
     EngineSmem* sm;
     unsigned long long* sm_sort = nullptr;  // component-table sort buffer (shared), if any
     int sm_sort_cap = 0;
@@ -147,6 +158,7 @@ struct Engine {
         epoch = 0;
         sweep_id = 0;
         scan_par = 0;
+        async_ok = true;
     }
 
     // Phase boundary: the time since the previous boundary is charged to phase `ph`.
@@ -403,9 +415,254 @@ struct Engine {
         accumulate(cnt, key);
     }
 
+    // ---------------- asynchronous levels-only sweep (whole grid) ----------------
+    // A levels-only sweep needs only the eccentricity of the root and the min (degree, id) vertex
+    // of the last level (Alg. 2), and both follow from the breadth-first distances alone, which
+    // are unique. So the sweep need not run level by level: it relaxes distances through a work
+    // queue with no grid barrier between levels, and the result is the same.
+    //   adist[v] = (~s) << 32 | dist for sweep stamp s: one 64-bit atomicMin both starts a new
+    //   sweep's value (a later sweep has a smaller high word) and keeps the shorter distance.
+    //   A warp takes 32 consecutive queue slots and polls them; each item (d, u) found relaxes
+    //   u's neighbours to d + 1, and every neighbour whose distance dropped is appended (slots
+    //   reserved with one atomic per warp round). An item made stale by a later improvement only
+    //   repeats relaxations that change nothing.
+    //   Items are handed over with release stores and acquire loads of their slots, so an item's
+    //   reservation happens before anything its consumer does.
+    //   Termination: every CTA publishes, with release, a monotone count of the items it has
+    //   finished, after reserving their children's slots. Let p be the sum of those counts (read
+    //   with acquire) and t the reserved-slot count read afterwards. Every counted item and every
+    //   child of one was reserved before that read, so if p == t the counted items are exactly
+    //   the slots [0, t). A reservation outside them would need a reserving item outside them
+    //   first, so none can ever happen: the queue is drained.
+    // Then two passes over the queue give the eccentricity (largest final distance), the size
+    // (items whose distance is final: one per vertex) and the last level's min (degree, id).
+    // Returns 1 when done, 0 on a failed wait or guard, -1 when the queue ran full (the caller
+    // repeats the sweep level by level).
+    __device__ int sweep_async(int root, int& ecc, unsigned long long& last_key, long long& reached) {
+        AsyncCtl* ac = a->actl;
+        unsigned long long* q = a->aq;
+        const unsigned Q = a->aq_cap;
+        const int s = ++sweep_id;
+        const unsigned long long tag = (unsigned long long)(~(unsigned)s) << 32;
+        const int b = blockIdx.x, B = gridDim.x;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        // queue emptied (slot 0 holds the root), counters cleared
+        const long long stride = (long long)B * blockDim.x;
+        for (long long i = 1 + (long long)b * blockDim.x + threadIdx.x; i < (long long)Q; i += stride) q[i] = kKeyMax;
+        if (threadIdx.x == 0) {
+            ac->proc[8 * b] = 0;
+            sm->aflag = 0;
+        }
+        if (b == 0 && threadIdx.x == 0) {
+            a->adist[root] = tag;
+            q[0] = (unsigned)root;
+            ac->head = 0;
+            ac->tail = 1ull;
+            ac->flag = 0;
+        }
+        if (!barrier()) return 0;
+        const unsigned long long t0 = globaltimer_ns();
+        unsigned base = 0, pend = 0;
+        unsigned long long item = kKeyMax;
+        bool have = false;
+        int idle = 0;
+        while (true) {
+            if (pend == 0) {
+                unsigned x = 0;
+                if (lane == 0) x = atomicAdd(&ac->head, 32u);
+                base = __shfl_sync(0xffffffffu, x, 0);
+                pend = 0xffffffffu;
+            }
+            const unsigned idx = base + (unsigned)lane;
+            if (!have && ((pend >> lane) & 1u) && idx < Q) {
+                item = ld_acquire_u64(q + idx);
+                have = item != kKeyMax;
+            }
+            const unsigned hm = __ballot_sync(0xffffffffu, have);
+            if (hm) {
+                relax_async(have, item, tag, q, Q);
+                __syncwarp();
+                if (lane == 0) red_release_add(&ac->proc[8 * b], (unsigned)__popc(hm));
+                pend &= ~hm;
+                have = false;
+                idle = 0;
+                continue;
+            }
+            ++idle;
+            int f = 0;
+            if (wid == 0) {
+                if (lane == 0) {
+                    f = ld_volatile(&ac->flag);
+                    if (ld_volatile(a->status) & (kErrTimeout | kErrInternal)) f |= 4;
+                    if (!f && (idle & 63) == 0 && (long long)(globaltimer_ns() - t0) > a->limit_ns) {
+                        atomicOr(a->status, kErrTimeout);
+                        f |= 4;
+                    }
+                }
+                f = __shfl_sync(0xffffffffu, f, 0);
+                if (!f && (idle & 7) == 0) {
+                    // termination test: finished counts (acquire), then the reserved count
+                    unsigned long long p = 0;
+                    for (int i = lane; i < B; i += 32) p += ld_acquire(&ac->proc[8 * i]);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+                    __syncwarp();
+                    unsigned long long t = 0;
+                    if (lane == 0) {
+                        __threadfence();
+                        t = ld_relaxed_u64(&ac->tail);
+                    }
+                    t = __shfl_sync(0xffffffffu, t, 0);
+                    if (p == t) {
+                        f = 1;
+                        if (lane == 0) atomicOr(&ac->flag, 1);
+                    }
+                }
+                if (f && lane == 0) *(volatile int*)&sm->aflag = f;
+            } else {
+                f = __shfl_sync(0xffffffffu, *(volatile int*)&sm->aflag, 0);
+            }
+            if (f) break;
+        }
+        __syncthreads();
+        if (!barrier()) return 0;
+        if (threadIdx.x == 0) sm->bc[0] = ld_volatile(&ac->flag);
+        __syncthreads();
+        const int flag = sm->bc[0];
+        __syncthreads();
+        if (flag & 2) return -1;
+        const unsigned long long t_all = ld_relaxed_u64(&ac->tail);
+        const unsigned T = t_all < (unsigned long long)Q ? (unsigned)t_all : Q;
+        // pass 1: size and eccentricity
+        unsigned maxd = 0;
+        int cnt = 0;
+        for (long long i = (long long)b * blockDim.x + threadIdx.x; i < (long long)T; i += stride) {
+            const unsigned long long it = __ldcg(q + i);
+            const int v = (int)(unsigned)(it & 0xffffffffu);
+            if (!in_graph(v)) {
+                fail_at(kSiteLevels, v);
+                continue;
+            }
+            const unsigned long long e = __ldcg(a->adist + v);
+            if ((e & 0xffffffff00000000ull) != tag) {
+                fail_at(kSiteLevels, v);
+                continue;
+            }
+            if ((unsigned)(it >> 32) == (unsigned)e) {
+                ++cnt;
+                maxd = max(maxd, (unsigned)e);
+            }
+        }
+        accumulate(cnt, 0xffffffffull - maxd);
+        ExResult r1;
+        if (!exchange(r1)) return 0;
+        ecc = (int)(0xffffffffu - (unsigned)r1.key);
+        reached = r1.total;
+        if (ecc < 0 || ecc > a->n) {
+            fail_at(kSiteLevels, ecc);
+            return 0;
+        }
+        // pass 2: min (degree, id) over the last level
+        unsigned long long key = kKeyMax;
+        for (long long i = (long long)b * blockDim.x + threadIdx.x; i < (long long)T; i += stride) {
+            const unsigned long long it = __ldcg(q + i);
+            if ((int)(unsigned)(it >> 32) != ecc) continue;
+            const int v = (int)(unsigned)(it & 0xffffffffu);
+            if (in_graph(v) && (int)(unsigned)__ldcg(a->adist + v) == ecc) {
+                const unsigned long long k = pack_key(__ldg(a->deg + v), v);
+                key = k < key ? k : key;
+            }
+        }
+        accumulate(0, key);
+        ExResult r2;
+        if (!exchange(r2)) return 0;
+        last_key = r2.key;
+        return 1;
+    }
+
+    // One round of the asynchronous sweep for the lanes holding an item (warp-collective).
+    __device__ void relax_async(bool have, unsigned long long item, unsigned long long tag, unsigned long long* q,
+                                unsigned Q) {
+        int u = have ? (int)(unsigned)(item & 0xffffffffu) : -1;
+        const unsigned nd = have ? (unsigned)(item >> 32) + 1u : 0u;
+        if (have && !in_graph(u)) {
+            fail_at(kSiteLevels, u);
+            u = -1;
+        }
+        const unsigned long long val = tag | nd;
+        int r[8];
+        int dg = 0;
+        if (u >= 0) {
+            load_row(u, r);
+            dg = r[7];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) r[k] = -1;
+        }
+        unsigned long long old[kEllNb];
+#pragma unroll
+        for (int k = 0; k < kEllNb; ++k) old[k] = k < dg ? atomicMin(a->adist + r[k], val) : val;
+        unsigned mask = 0;
+#pragma unroll
+        for (int k = 0; k < kEllNb; ++k) mask |= (old[k] > val ? 1u : 0u) << k;
+        push_async(mask, r, nd, q, Q);
+        // neighbours beyond the padded row (degree > 7), 8 per round
+        const int extra = dg > kEllNb ? dg - kEllNb : 0;
+        const int rounds = __reduce_max_sync(0xffffffffu, (unsigned)((extra + 7) >> 3));
+        const int rp = extra ? __ldg(a->rowptr + u) : 0;
+        for (int j = 0; j < rounds; ++j) {
+            int w[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int p = kEllNb + 8 * j + k;
+                w[k] = p < dg ? __ldg(a->adj + rp + p) : -1;
+            }
+            unsigned long long o2[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) o2[k] = w[k] >= 0 ? atomicMin(a->adist + w[k], val) : val;
+            unsigned m2 = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) m2 |= (o2[k] > val ? 1u : 0u) << k;
+            push_async(m2, w, nd, q, Q);
+        }
+    }
+
+    // Appends the vertices w[k] (bit k of mask) with distance nd: one slot reservation per warp.
+    __device__ void push_async(unsigned mask, const int (&w)[8], unsigned nd, unsigned long long* q, unsigned Q) {
+        const int lane = threadIdx.x & 31;
+        const int c = __popc(mask);
+        const int incl = warp_incl_scan(c);
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        if (tot == 0) return;
+        unsigned long long x = 0;
+        if (lane == 0) x = atomicAdd(&a->actl->tail, (unsigned long long)tot);
+        unsigned long long pos = __shfl_sync(0xffffffffu, x, 0) + (unsigned long long)(incl - c);
+        __syncwarp();  // the reservation is ordered before every lane's release store below
+        bool full = false;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (mask & (1u << k)) {
+                if (pos < (unsigned long long)Q) {
+                    prefetch_row(w[k]);
+                    st_release_u64(q + pos, ((unsigned long long)nd << 32) | (unsigned)w[k]);
+                } else {
+                    full = true;
+                }
+                ++pos;
+            }
+        if (__any_sync(0xffffffffu, full) && lane == 0) atomicOr(&a->actl->flag, 2);
+    }
+
     // Levels-only sweep from root. On return: ecc, the min (degree, id) key of the last level and
     // the number of vertices reached (the component's size).
     __device__ bool sweep_levels(int root, int& ecc, unsigned long long& last_key, long long& reached) {
+        if constexpr (kAsync) {
+            if (a->adist && async_ok) {
+                const int rc = sweep_async(root, ecc, last_key, reached);
+                if (rc >= 0) return rc == 1;
+                async_ok = false;  // the queue ran full: this and later sweeps run level by level
+            }
+        }
         Ctl* c = a->ctl;
         const int s = ++sweep_id;
         const int b = cta_rank(), B = cta_count();

@@ -65,6 +65,18 @@ struct alignas(128) Ctl {
     ExSlot slots[2][kMaxGridBlocks];  // exchange slots, double-buffered by epoch parity
 };
 
+// Counters of the asynchronous levels-only sweep (one per ordering), each hot word on its own
+// 128-byte line. proc[8 b] = items CTA b has finished, a monotone count published with release.
+struct alignas(128) AsyncCtl {
+    unsigned int head;       // next queue slot handed out (32 per warp)
+    unsigned int pad0[31];
+    unsigned long long tail; // queue slots reserved by producers
+    unsigned long long pad1[15];
+    int flag;                // bit 0: the sweep has finished; bit 1: the queue ran full
+    int pad2[31];
+    unsigned int proc[kMaxGridBlocks * 8];
+};
+
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -78,6 +90,22 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
 }
 
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 
 // Coherent (L2) load for data written by other CTAs during this kernel.
 __device__ __forceinline__ int ldcg(const int* p) { return __ldcg(p); }

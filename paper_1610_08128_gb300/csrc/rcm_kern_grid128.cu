@@ -1,0 +1,10 @@
+// rcm_kern_grid128.cu -- instantiates the persistent grid kernel of rcm_single_kernels.cuh for CTAs of 128 threads
+// (one translation unit per width, so the widths compile in parallel).
+#define RCM_KERNEL_DEFINITIONS
+#include "rcm_single_kernels.cuh"
+
+namespace rcm {
+
+template __global__ void k_rcm_single<128, false>(EngineArgs, int);
+
+}  // namespace rcm

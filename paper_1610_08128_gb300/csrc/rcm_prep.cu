@@ -15,7 +15,8 @@ namespace rcm {
 
 __global__ void k_degree_validate(int n, int nnz, const int* __restrict__ rowptr, const int* __restrict__ colidx,
                                   int* __restrict__ deg, unsigned long long* __restrict__ claim, int* __restrict__ vis,
-                                  int* __restrict__ bigrows, Ctl* ctl, int small_max) {
+                                  int* __restrict__ bigrows, Ctl* ctl, int small_max,
+                                  unsigned long long* __restrict__ adist) {
     __shared__ int s_max;
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
@@ -41,6 +42,7 @@ __global__ void k_degree_validate(int n, int nnz, const int* __restrict__ rowptr
         deg[v] = d;
         claim[v] = ~0ull;
         vis[v] = 0;
+        if (adist) adist[v] = ~0ull;
         local_max = max(local_max, d);
     }
     atomicMax(&s_max, local_max);

@@ -111,10 +111,11 @@ __device__ __forceinline__ void sort_big_row_cta(int v, const int* __restrict__ 
 }
 
 // nnz: the stored-entry count the caller sized its buffers for; rowptr[n] must equal it, and no
-// row is read beyond it.
+// row is read beyond it. adist (may be null): the asynchronous sweeps' per-vertex words, cleared.
 __global__ void k_degree_validate(int n, int nnz, const int* __restrict__ rowptr, const int* __restrict__ colidx,
                                   int* __restrict__ deg, unsigned long long* __restrict__ claim, int* __restrict__ vis,
-                                  int* __restrict__ bigrows, Ctl* ctl, int small_max);
+                                  int* __restrict__ bigrows, Ctl* ctl, int small_max,
+                                  unsigned long long* __restrict__ adist = nullptr);
 
 // small_max (<= kSmallRowMax): rows with at most this many stored entries are sorted here, one
 // thread per row; k_degree_validate lists the longer ones for k_sort_rows_big with the same value.

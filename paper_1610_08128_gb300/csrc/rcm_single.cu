@@ -1,181 +1,16 @@
-// rcm_single.cu -- RCM ordering of one graph: the preprocessing launches (degree + validation,
-// (degree, id)-sorted adjacency) and one cooperative persistent kernel that runs every sweep and
-// every breadth-first level on the device (Engine<false> in rcm_engine.cuh).
+// rcm_single.cu -- RCM ordering of one graph, host side: workspace layout, launch shape, and the
+// launches (degree + validation, (degree, id)-sorted adjacency, then one persistent kernel that
+// runs every sweep and every breadth-first level on the device; see rcm_single_kernels.cuh).
 #include <algorithm>
 #include <mutex>
 
 #include "rcm_host.hpp"
-#include "rcm_engine.cuh"
-#include "rcm_single.cuh"
 #include "rcm_internal.cuh"
 #include "rcm_prep.cuh"
+#include "rcm_single.cuh"
+#include "rcm_single_kernels.cuh"
 
 namespace rcm {
-
-template <int kThreads>
-__global__ void __launch_bounds__(kThreads, 1) k_rcm_single(EngineArgs args, int stall) {
-    __shared__ EngineSmem smem;
-    __shared__ int s_item;
-    extern __shared__ unsigned long long s_sort[];  // component-table sort (kCompSmem entries)
-    Ctl* ctl = args.ctl;
-    if (ld_volatile(&ctl->status) & kErrBadCsr) return;
-    if (stall && blockIdx.x == 0) return;  // test hook: the other CTAs' first wait runs out
-    const int n = args.n;
-    Engine<false> e;
-    e.init(args, &smem);
-    int Z = 0;
-    if (!e.label_isolated(Z)) return;
-    e.stat_add(kStIsolated, Z);
-    e.stat_add(kStComponents, Z);
-    int nv = Z;
-    int C = -1;
-    bool first = true, tried = false;
-    while (nv < n) {
-        if (!first && !tried && args.cc_cap > 0) {
-            // more than one component: order them concurrently (one attempt)
-            tried = true;
-            C = e.cc_prepare(nv, s_sort, kCompSmem);
-            if (C == -2) return;
-            if (C > 0) break;
-        }
-        unsigned long long k0;
-        if (!e.next_start(k0)) return;
-        if (k0 == kKeyMax) {
-            e.fail(kErrInternal);
-            return;
-        }
-        int size;
-        // the first component's first sweep shows whether it spans everything left
-        const long long left = (first && args.cc_cap > 0) ? (long long)(n - nv) : -1;
-        first = false;
-        if (!e.component((int)(unsigned)(k0 & 0xffffffffu), nv, size, left)) return;
-        if (size < 0) continue;  // more components: the next iteration prepares them all
-        nv += size;
-    }
-    if (C > 0) {
-        // large components on the whole grid, one after another
-        for (int i = 0; i < C; ++i) {
-            const int4 t = __ldcg(args.cc_tab + i);
-            if (!e.tab_ok(t, nv)) {
-                e.fail_at(kSiteTable, i);
-                return;
-            }
-            if (t.z < args.cc_big) continue;
-            int size;
-            if (!e.component(t.x, t.y, size)) return;
-            if (size != t.z) {
-                e.fail(kErrInternal);
-                return;
-            }
-        }
-    }
-    // statistics: CTA 0 adds the grid part; CTAs add their own parts below (ctl->stats starts at 0)
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        for (int i = 0; i < 8; ++i) {
-            if (i == kStMaxEcc) atomicMax((unsigned long long*)&ctl->stats[i], (unsigned long long)smem.st[i]);
-            else atomicAdd((unsigned long long*)&ctl->stats[i], (unsigned long long)smem.st[i]);
-        }
-        for (int i = 0; i < 8; ++i) ctl->phase_ns[i] = smem.prof[i];
-    }
-    if (C <= 0) return;
-    // the other components, one per CTA (CTA barriers only)
-    __syncthreads();
-    Engine<true> ec;
-    bool any = false;
-    while (true) {
-        if (threadIdx.x == 0) s_item = atomicAdd(&ctl->work_next, 1);
-        __syncthreads();
-        const int i = s_item;
-        __syncthreads();
-        if (i >= C) break;
-        const int4 t = __ldcg(args.cc_tab + i);
-        if (!e.tab_ok(t, nv)) {
-            e.fail_at(kSiteTable, i);
-            return;
-        }
-        if (t.z >= args.cc_big) continue;
-        EngineArgs ca = args;
-        ca.qa = args.qa + t.y;
-        ca.qb = args.qb + t.y;
-        ca.boff = args.boff + t.y;
-        ca.narrow_thr = 0x7fffffff;
-        ca.obits = claim_order_bits(t.z);
-        ca.profile = 0;
-        if (!any) {
-            ec.init(ca, &smem);
-            // visit stamps of these engines stay clear of the grid engine's (whose first sweep may
-            // already have stamped the first component)
-            ec.sweep_id = 1 << 24;
-            any = true;
-        } else {
-            __syncthreads();
-            if (threadIdx.x == 0) smem.args = ca;
-            __syncthreads();
-        }
-        int size;
-        if (!ec.component(t.x, t.y, size)) return;
-        if (size != t.z) {
-            ec.fail(kErrInternal);
-            return;
-        }
-    }
-    if (any && threadIdx.x == 0) {
-        for (int i = 0; i < 8; ++i) {
-            if (i == kStMaxEcc) atomicMax((unsigned long long*)&ctl->stats[i], (unsigned long long)smem.st[i]);
-            else if (i != kStIsolated && i != kStGrid) atomicAdd((unsigned long long*)&ctl->stats[i], (unsigned long long)smem.st[i]);
-        }
-    }
-}
-
-
-// Graphs of at most kSmallMaxN vertices: one CTA orders the whole graph with its claims, visit
-// stamps and padded rows in shared memory (Engine<true, true>), so every level's row reads and
-// atomics stay inside one SM instead of going to L2.
-constexpr int kSmallMaxN = 4608;
-constexpr int kSmallSort = 256;  // component tables sorted in shared memory up to this size
-
-// Shared-memory layout: claims (8n bytes) at 0, stamps (4n) and then the padded rows (32n, read
-// and written as 16-byte int4) each at the next 16-byte boundary.
-static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
-static size_t small_vis_off(int n) { return align16(8 * (size_t)n); }
-static size_t small_ell_off(int n) { return align16(small_vis_off(n) + 4 * (size_t)n); }
-static size_t small_smem_bytes(int n) { return small_ell_off(n) + 32 * (size_t)n; }
-
-// kThreads: narrow graphs (a few dozen vertices per level) run best on small CTAs, whose barriers,
-// scans and reductions are cheap.
-template <int kThreads>
-__global__ void __launch_bounds__(kThreads, 1) k_rcm_small(EngineArgs args, int vis_off, int ell_off) {
-    extern __shared__ __align__(16) unsigned long long s_state[];
-    __shared__ EngineSmem smem;
-    __shared__ unsigned long long s_sort[kSmallSort + kSmallSort / 2];
-    Ctl* ctl = args.ctl;
-    if (ld_volatile(&ctl->status) & kErrBadCsr) return;
-    const int n = args.n;
-    unsigned long long* claim = s_state;
-    int* vis = (int*)((char*)s_state + vis_off);
-    int4* ell = (int4*)((char*)s_state + ell_off);
-    for (int i = threadIdx.x; i < n; i += kThreads) {
-        claim[i] = kClaimNone;
-        vis[i] = 0;
-        ell[2 * i] = __ldg(args.ell + 2 * (size_t)i);
-        ell[2 * i + 1] = __ldg(args.ell + 2 * (size_t)i + 1);
-    }
-    __syncthreads();
-    EngineArgs a = args;
-    a.claim = claim;
-    a.vis = vis;
-    a.ell = ell;
-    Engine<true, true> e;
-    e.init(a, &smem);
-    e.sm_sort = s_sort;
-    e.sm_sort_cap = kSmallSort;
-    e.run();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < 8; ++i) ctl->stats[i] = smem.st[i];
-        for (int i = 0; i < 8; ++i) ctl->phase_ns[i] = smem.prof[i];
-    }
-}
 
 // ------------------------------------------------------------------------------------------
 // host side
@@ -186,7 +21,7 @@ constexpr int kComponentOnGrid = 1 << 18;
 
 // with_cc: also the arrays of the concurrent-components pass (the fixed no-allocation workspace
 // leaves them out and orders components one by one).
-SingleLayout single_layout(long long n, long long nnz, bool with_cc) {
+SingleLayout single_layout(long long n, long long nnz, bool with_cc, bool with_async) {
     SingleLayout L;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -202,6 +37,11 @@ SingleLayout single_layout(long long n, long long nnz, bool with_cc) {
     L.bigrows = take(sizeof(int) * (size_t)std::max(n, 1LL));
     L.adj = take(sizeof(int) * (size_t)std::max(nnz, 1LL));
     L.ell = take(sizeof(int4) * 2 * (size_t)std::max(n, 1LL));
+    L.adist = L.actl = 0;
+    if (with_async) {
+        L.adist = take(sizeof(unsigned long long) * (size_t)std::max(n, 1LL));
+        L.actl = take(sizeof(AsyncCtl));
+    }
     L.cc_cap = with_cc ? (int)std::min<long long>(std::max(n, 1LL), kMaxComps) : 0;
     if (!with_cc) {
         L.cc_size = L.cc_key = L.cc_roots = L.cc_gkey = L.cc_gidx = L.cc_tab = 0;
@@ -220,6 +60,7 @@ SingleLayout single_layout(long long n, long long nnz, bool with_cc) {
     return L;
 }
 
+// CTAs per SM of each kernel: widths 32..1024 level by level (0..5), 512 with asynchronous sweeps (6)
 static int g_single_blocks_per_sm[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
 static std::mutex g_single_mu;
 
@@ -235,27 +76,31 @@ static int threads_index(int threads) {
     return -1;
 }
 
-static const void* single_kernel(int threads) {
+// async: the instantiation with asynchronous levels-only sweeps (512 threads only)
+static const void* single_kernel(int threads, bool async = false) {
+    if (async) return (const void*)k_rcm_single<512, true>;
     switch (threads) {
-        case 32: return (const void*)k_rcm_single<32>;
-        case 64: return (const void*)k_rcm_single<64>;
-        case 128: return (const void*)k_rcm_single<128>;
-        case 256: return (const void*)k_rcm_single<256>;
-        case 1024: return (const void*)k_rcm_single<1024>;
+        case 32: return (const void*)k_rcm_single<32, false>;
+        case 64: return (const void*)k_rcm_single<64, false>;
+        case 128: return (const void*)k_rcm_single<128, false>;
+        case 256: return (const void*)k_rcm_single<256, false>;
+        case 1024: return (const void*)k_rcm_single<1024, false>;
     }
-    return (const void*)k_rcm_single<512>;
+    return (const void*)k_rcm_single<512, false>;
 }
 
 constexpr int kSingleDynSmem = (int)((sizeof(unsigned long long) + sizeof(int)) * kCompSmem);
 
-static int single_blocks_per_sm(int threads) {
+static int single_blocks_per_sm(int threads, bool async = false) {
     std::lock_guard<std::mutex> g(g_single_mu);
-    const int idx = threads_index(threads);
+    if (async && threads != 512) return 0;
+    const int idx = async ? 6 : threads_index(threads);
     if (idx < 0) return 0;  // not a supported block size (the options check rejects it first)
     if (g_single_blocks_per_sm[idx] < 0) {
         int b = 0;
-        cudaFuncSetAttribute(single_kernel(threads), cudaFuncAttributeMaxDynamicSharedMemorySize, kSingleDynSmem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, single_kernel(threads), threads, kSingleDynSmem);
+        const void* k = single_kernel(threads, async);
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSingleDynSmem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, threads, kSingleDynSmem);
         g_single_blocks_per_sm[idx] = b;
         cudaFuncSetAttribute(k_sort_rows_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(unsigned long long) * kBigRowSmem));
@@ -266,12 +111,13 @@ static int single_blocks_per_sm(int threads) {
 static int g_cluster_max = -1;
 
 int single_cluster_max() {
-    if (single_blocks_per_sm(512) <= 0) return 0;
+    if (single_blocks_per_sm(512) <= 0 || single_blocks_per_sm(512, true) <= 0) return 0;
     std::lock_guard<std::mutex> g(g_single_mu);
     if (g_cluster_max < 0) {
         g_cluster_max = 0;
         const void* k = single_kernel(512);
         cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(single_kernel(512, true), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         for (int c : {16, 8}) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(c);
@@ -342,7 +188,9 @@ rcm_status single_launch(int n, const rcm_options& o, SingleLaunch* out) {
     }
     sl.threads = o.block_threads ? o.block_threads : 512;
     if (threads_index(sl.threads) < 0) return RCM_ERR_INVALID_ARG;
-    const int per_sm = single_blocks_per_sm(sl.threads);
+    sl.async = o.async_sweeps > 0;
+    if (sl.async && sl.threads != 512) return RCM_ERR_INVALID_ARG;
+    const int per_sm = single_blocks_per_sm(sl.threads, sl.async);
     if (per_sm <= 0) return RCM_ERR_CUDA;
     sl.cluster = o.cluster != 0;
     if (sl.cluster) {
@@ -370,6 +218,7 @@ rcm_status single_launch(int n, const rcm_options& o, SingleLaunch* out) {
     sl.fused = o.fused_sweeps >= 0 ? 1 : 0;
     sl.profile = o.profile_phases ? 1 : 0;
     sl.stall = o.debug_stall_barrier ? 1 : 0;
+    sl.async_slots = o.debug_async_slots;
     *out = sl;
     return RCM_OK;
 }
@@ -385,6 +234,9 @@ cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* c
     int* bigrows = (int*)(base + L.bigrows);
     int* adj = (int*)(base + L.adj);
     int4* ell = (int4*)(base + L.ell);
+    // the asynchronous sweeps need their words in the layout; without them the sweeps run level by level
+    const bool async = sl.async && !sl.small && L.adist != 0;
+    unsigned long long* adist = async ? (unsigned long long*)(base + L.adist) : nullptr;
 
     cudaError_t e = cudaSuccess;
     if (ev) e = cudaEventRecord(ev[0], s);
@@ -393,7 +245,7 @@ cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* c
         const int pb = 256;
         const int pgrid = (int)std::min<long long>((n + pb - 1) / pb, (long long)di.sms * 16);
         k_degree_validate<<<std::max(pgrid, 1), pb, 0, s>>>(n, (int)nnz, rowptr, colidx, deg, claim, vis, bigrows, ctl,
-                                                           kSmallRowMax);
+                                                           kSmallRowMax, adist);
         k_sort_rows_small<<<std::max(pgrid, 1), pb, 0, s>>>(n, rowptr, colidx, deg, adj, ell, ctl, kSmallRowMax);
         // rows longer than kSmallRowMax entries number at most nnz / (kSmallRowMax + 1)
         const int big_grid = (int)std::max<long long>(1, std::min<long long>(2LL * di.sms, nnz / (kSmallRowMax + 1)));
@@ -439,6 +291,14 @@ cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* c
     }
     args.cc_cap = L.cc_cap;
     args.cc_big = kComponentOnGrid;
+    // work queue of the asynchronous sweeps: pool4 as 2n 64-bit slots (the level-by-level
+    // frontier buffers and the union-find parents are not in use while such a sweep runs)
+    args.adist = adist;
+    args.aq = async ? (unsigned long long*)pool4 : nullptr;
+    args.actl = async ? (AsyncCtl*)(base + L.actl) : nullptr;
+    long long slots = std::min<long long>(2LL * n, 1LL << 31);
+    if (sl.async_slots > 0) slots = std::min<long long>(slots, sl.async_slots);
+    args.aq_cap = async ? (unsigned)slots : 0u;
     int stall = sl.stall;
     void* kargs[] = {&args, &stall};
     if (sl.small) {
@@ -458,9 +318,9 @@ cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* c
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelExC(&cfg, single_kernel(sl.threads), kargs);
+        e = cudaLaunchKernelExC(&cfg, single_kernel(sl.threads, async), kargs);
     } else {
-        e = cudaLaunchCooperativeKernel(single_kernel(sl.threads), dim3(sl.blocks), dim3(sl.threads), kargs,
+        e = cudaLaunchCooperativeKernel(single_kernel(sl.threads, async), dim3(sl.blocks), dim3(sl.threads), kargs,
                                         kSingleDynSmem, s);
     }
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
@@ -475,7 +335,7 @@ rcm_status order_single(int32_t n, int64_t nnz, const int32_t* rowptr, const int
     SingleLaunch sl;
     rcm_status st = single_launch(n, o, &sl);
     if (st != RCM_OK) return st;
-    const SingleLayout L = single_layout(n, nnz);
+    const SingleLayout L = single_layout(n, nnz, true, sl.async && !sl.small);
     void* ws = nullptr;
     st = ws_alloc(&ws, L.total, s);
     if (st != RCM_OK) return st;

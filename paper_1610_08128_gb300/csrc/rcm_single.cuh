@@ -9,11 +9,15 @@ namespace rcm {
 // Byte offsets of the one-graph workspace, each 256-byte aligned; total = bytes to allocate.
 // cc_cap = components the concurrent-components pass handles (0 = that pass is off and the
 // component arrays are absent).
+// adist / actl: the asynchronous levels-only sweeps' distance words and counters (0 = absent; the
+// sweeps' work queue reuses the frontier buffers of pool4).
 struct SingleLayout {
-    size_t ctl, pool4, deg, claim, vis, bigrows, adj, ell, cc_size, cc_key, cc_roots, cc_gkey, cc_gidx, cc_tab, total;
+    size_t ctl, pool4, deg, claim, vis, bigrows, adj, ell, cc_size, cc_key, cc_roots, cc_gkey, cc_gidx, cc_tab,
+        adist, actl, total;
     int cc_cap;
 };
-SingleLayout single_layout(long long n, long long nnz, bool with_cc = true);
+// with_async: include the asynchronous sweeps' arrays (only calls that ask for those sweeps).
+SingleLayout single_layout(long long n, long long nnz, bool with_cc = true, bool with_async = false);
 
 // Launch shape of the engine.
 //   small = true:    one CTA holding the graph's claims, stamps and rows in shared memory.
@@ -30,6 +34,8 @@ struct SingleLaunch {
     int fused = 1;
     int profile = 0;
     int stall = 0;
+    bool async = false;          // levels-only sweeps through the asynchronous work queue
+    int async_slots = 0;         // its capacity (0 = 2n)
 };
 
 // Derives the launch shape from options for a graph of n vertices; RCM_ERR_INVALID_ARG for

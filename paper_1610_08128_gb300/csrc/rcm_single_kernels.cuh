@@ -1,0 +1,198 @@
+// rcm_single_kernels.cuh -- the one-graph kernels: k_rcm_single (the persistent grid engine) and
+// k_rcm_small (one CTA with the graph's traversal state in shared memory), templated on the CTA
+// width. Their definitions are compiled only in the translation units that instantiate them
+// (rcm_kern_*.cu, built in parallel); everyone else sees declarations and extern instantiations.
+#pragma once
+
+#include "rcm_engine.cuh"
+#include "rcm_internal.cuh"
+
+namespace rcm {
+
+// Graphs of at most kSmallMaxN vertices: one CTA orders the whole graph with its claims, visit
+// stamps and padded rows in shared memory (Engine<true, true>), so every level's row reads and
+// atomics stay inside one SM instead of going to L2.
+constexpr int kSmallMaxN = 4608;
+constexpr int kSmallSort = 256;  // component tables sorted in shared memory up to this size
+
+// Shared-memory layout: claims (8n bytes) at 0, stamps (4n) and then the padded rows (32n, read
+// and written as 16-byte int4) each at the next 16-byte boundary.
+inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+inline size_t small_vis_off(int n) { return align16(8 * (size_t)n); }
+inline size_t small_ell_off(int n) { return align16(small_vis_off(n) + 4 * (size_t)n); }
+inline size_t small_smem_bytes(int n) { return small_ell_off(n) + 32 * (size_t)n; }
+
+// kAsync: the engine with asynchronous levels-only sweeps (instantiated for 512 threads only).
+template <int kThreads, bool kAsync>
+__global__ void __launch_bounds__(kThreads, 1) k_rcm_single(EngineArgs args, int stall);
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads, 1) k_rcm_small(EngineArgs args, int vis_off, int ell_off);
+
+#ifndef RCM_KERNEL_DEFINITIONS
+extern template __global__ void k_rcm_single<32, false>(EngineArgs, int);
+extern template __global__ void k_rcm_single<64, false>(EngineArgs, int);
+extern template __global__ void k_rcm_single<128, false>(EngineArgs, int);
+extern template __global__ void k_rcm_single<256, false>(EngineArgs, int);
+extern template __global__ void k_rcm_single<512, false>(EngineArgs, int);
+extern template __global__ void k_rcm_single<1024, false>(EngineArgs, int);
+extern template __global__ void k_rcm_single<512, true>(EngineArgs, int);
+extern template __global__ void k_rcm_small<32>(EngineArgs, int, int);
+extern template __global__ void k_rcm_small<64>(EngineArgs, int, int);
+extern template __global__ void k_rcm_small<128>(EngineArgs, int, int);
+extern template __global__ void k_rcm_small<256>(EngineArgs, int, int);
+extern template __global__ void k_rcm_small<512>(EngineArgs, int, int);
+#else
+template <int kThreads, bool kAsync>
+__global__ void __launch_bounds__(kThreads, 1) k_rcm_single(EngineArgs args, int stall) {
+    __shared__ EngineSmem smem;
+    __shared__ int s_item;
+    extern __shared__ unsigned long long s_sort[];  // component-table sort (kCompSmem entries)
+    Ctl* ctl = args.ctl;
+    if (ld_volatile(&ctl->status) & kErrBadCsr) return;
+    if (stall && blockIdx.x == 0) return;  // test hook: the other CTAs' first wait runs out
+    const int n = args.n;
+    Engine<false, false, kAsync> e;
+    e.init(args, &smem);
+    int Z = 0;
+    if (!e.label_isolated(Z)) return;
+    e.stat_add(kStIsolated, Z);
+    e.stat_add(kStComponents, Z);
+    int nv = Z;
+    int C = -1;
+    bool first = true, tried = false;
+    while (nv < n) {
+        if (!first && !tried && args.cc_cap > 0) {
+            // more than one component: order them concurrently (one attempt)
+            tried = true;
+            C = e.cc_prepare(nv, s_sort, kCompSmem);
+            if (C == -2) return;
+            if (C > 0) break;
+        }
+        unsigned long long k0;
+        if (!e.next_start(k0)) return;
+        if (k0 == kKeyMax) {
+            e.fail(kErrInternal);
+            return;
+        }
+        int size;
+        // the first component's first sweep shows whether it spans everything left
+        const long long left = (first && args.cc_cap > 0) ? (long long)(n - nv) : -1;
+        first = false;
+        if (!e.component((int)(unsigned)(k0 & 0xffffffffu), nv, size, left)) return;
+        if (size < 0) continue;  // more components: the next iteration prepares them all
+        nv += size;
+    }
+    if (C > 0) {
+        // large components on the whole grid, one after another
+        for (int i = 0; i < C; ++i) {
+            const int4 t = __ldcg(args.cc_tab + i);
+            if (!e.tab_ok(t, nv)) {
+                e.fail_at(kSiteTable, i);
+                return;
+            }
+            if (t.z < args.cc_big) continue;
+            int size;
+            if (!e.component(t.x, t.y, size)) return;
+            if (size != t.z) {
+                e.fail(kErrInternal);
+                return;
+            }
+        }
+    }
+    // statistics: CTA 0 adds the grid part; CTAs add their own parts below (ctl->stats starts at 0)
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int i = 0; i < 8; ++i) {
+            if (i == kStMaxEcc) atomicMax((unsigned long long*)&ctl->stats[i], (unsigned long long)smem.st[i]);
+            else atomicAdd((unsigned long long*)&ctl->stats[i], (unsigned long long)smem.st[i]);
+        }
+        for (int i = 0; i < 8; ++i) ctl->phase_ns[i] = smem.prof[i];
+    }
+    if (C <= 0) return;
+    // the other components, one per CTA (CTA barriers only)
+    __syncthreads();
+    Engine<true> ec;
+    bool any = false;
+    while (true) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&ctl->work_next, 1);
+        __syncthreads();
+        const int i = s_item;
+        __syncthreads();
+        if (i >= C) break;
+        const int4 t = __ldcg(args.cc_tab + i);
+        if (!e.tab_ok(t, nv)) {
+            e.fail_at(kSiteTable, i);
+            return;
+        }
+        if (t.z >= args.cc_big) continue;
+        EngineArgs ca = args;
+        ca.qa = args.qa + t.y;
+        ca.qb = args.qb + t.y;
+        ca.boff = args.boff + t.y;
+        ca.narrow_thr = 0x7fffffff;
+        ca.obits = claim_order_bits(t.z);
+        ca.profile = 0;
+        if (!any) {
+            ec.init(ca, &smem);
+            // visit stamps of these engines stay clear of the grid engine's (whose first sweep may
+            // already have stamped the first component)
+            ec.sweep_id = 1 << 24;
+            any = true;
+        } else {
+            __syncthreads();
+            if (threadIdx.x == 0) smem.args = ca;
+            __syncthreads();
+        }
+        int size;
+        if (!ec.component(t.x, t.y, size)) return;
+        if (size != t.z) {
+            ec.fail(kErrInternal);
+            return;
+        }
+    }
+    if (any && threadIdx.x == 0) {
+        for (int i = 0; i < 8; ++i) {
+            if (i == kStMaxEcc) atomicMax((unsigned long long*)&ctl->stats[i], (unsigned long long)smem.st[i]);
+            else if (i != kStIsolated && i != kStGrid) atomicAdd((unsigned long long*)&ctl->stats[i], (unsigned long long)smem.st[i]);
+        }
+    }
+}
+
+
+// kThreads: narrow graphs (a few dozen vertices per level) run best on small CTAs, whose barriers,
+// scans and reductions are cheap.
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads, 1) k_rcm_small(EngineArgs args, int vis_off, int ell_off) {
+    extern __shared__ __align__(16) unsigned long long s_state[];
+    __shared__ EngineSmem smem;
+    __shared__ unsigned long long s_sort[kSmallSort + kSmallSort / 2];
+    Ctl* ctl = args.ctl;
+    if (ld_volatile(&ctl->status) & kErrBadCsr) return;
+    const int n = args.n;
+    unsigned long long* claim = s_state;
+    int* vis = (int*)((char*)s_state + vis_off);
+    int4* ell = (int4*)((char*)s_state + ell_off);
+    for (int i = threadIdx.x; i < n; i += kThreads) {
+        claim[i] = kClaimNone;
+        vis[i] = 0;
+        ell[2 * i] = __ldg(args.ell + 2 * (size_t)i);
+        ell[2 * i + 1] = __ldg(args.ell + 2 * (size_t)i + 1);
+    }
+    __syncthreads();
+    EngineArgs a = args;
+    a.claim = claim;
+    a.vis = vis;
+    a.ell = ell;
+    Engine<true, true> e;
+    e.init(a, &smem);
+    e.sm_sort = s_sort;
+    e.sm_sort_cap = kSmallSort;
+    e.run();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 8; ++i) ctl->stats[i] = smem.st[i];
+        for (int i = 0; i < 8; ++i) ctl->phase_ns[i] = smem.prof[i];
+    }
+}
+#endif
+
+}  // namespace rcm

@@ -40,6 +40,8 @@ class rcm_options(ctypes.Structure):
         ("profile_phases", ctypes.c_int32),
         ("cluster", ctypes.c_int32),
         ("executor", ctypes.c_int32),
+        ("async_sweeps", ctypes.c_int32),
+        ("debug_async_slots", ctypes.c_int32),
     ]
 
 

@@ -74,3 +74,36 @@ def test_binding_refuses_missing_library(monkeypatch, tmp_path):
 def test_kernels_are_sm103a(lib):
     """The build targets exactly one architecture: compute_103a -> sm_103a."""
     assert build_mod.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_binding_structures_match_the_header(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets of its C declaration
+    in include/rcm.h (compiled here with the host C compiler)."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    from paper_1610_08128_gb300 import rcm
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no host C compiler")
+    structs = [rcm.rcm_options, rcm.rcm_batch_options, rcm.rcm_server_options, rcm.rcm_stats, rcm.rcm_server_stats]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rcm.h"', "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in st._fields_:
+            lines.append(f'printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for st in structs:
+        name = st.__name__
+        assert got[(name, "size")] == ctypes.sizeof(st), name
+        for f, _ in st._fields_:
+            assert got[(name, f)] == getattr(st, f).offset, (name, f)

@@ -154,6 +154,12 @@ OPTION_SETS = [
     {"cluster": 1, "grid_blocks": 8},
     {"cluster": 1, "grid_blocks": 2, "narrow_threshold": -1},
     {"executor": 1},                     # persistent grid even for graphs the shared-memory CTA takes
+    {"executor": 1, "async_sweeps": 1},  # levels-only sweeps through the asynchronous work queue
+    {"async_sweeps": 1, "grid_blocks": 3},
+    {"async_sweeps": 1, "narrow_threshold": -1},
+    {"async_sweeps": 1, "cluster": 1, "grid_blocks": 4},
+    {"async_sweeps": -1, "executor": 1},
+    {"executor": 1, "async_sweeps": 1, "debug_async_slots": 16},   # queue runs full: level-by-level fallback
 ]
 
 
@@ -163,6 +169,31 @@ def test_options_do_not_change_the_result(opts):
               synth.random_graph(3000, 4000, 9)] + small_graphs(25, 200, 102)
     for g in graphs:
         assert_parity(g, opts)
+
+
+def test_async_sweeps_on_large_graphs():
+    """Levels-only sweeps through the asynchronous work queue and level by level give the oracle's
+    order and the same sweep counts on large graphs: a 3D grid, a high-diameter 2D grid, a mesh
+    with components, a deep tree and a path. A queue that runs full falls back to level by level
+    with the same result; the asynchronous engine exists for 512-thread CTAs only."""
+    graphs = [synth.grid((80, 80, 80), seed=71), synth.grid((700, 700), seed=72), synth.c3_mesh(300000),
+              synth.random_tree(200000, 73), synth.path(150000, seed=74)]
+    keys = ("components", "sweeps", "traversals", "levels", "max_ecc", "isolated")
+    for g in graphs:
+        want = oracle.rcm(g.n, g.rowptr, g.colidx)
+        a, sa = gpu_perm(g, {"async_sweeps": 1}, with_stats=True)
+        b, sb = gpu_perm(g, {"async_sweeps": -1}, with_stats=True)
+        assert np.array_equal(a, want)
+        assert np.array_equal(b, want)
+        assert {k: sa[k] for k in keys} == {k: sb[k] for k in keys}
+    g = graphs[0]
+    assert np.array_equal(gpu_perm(g, {"async_sweeps": 1, "debug_async_slots": 1000}), oracle.rcm(g.n, g.rowptr, g.colidx))
+    rcm = rcm_mod()
+    rp, ci = to_dev(g)
+    o = rcm.rcm_options()
+    o.async_sweeps, o.block_threads = 1, 256
+    pm = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    assert rcm.rcm_order_ex(g.n, rp, ci, pm, o, None) == rcm.RCM_ERR_INVALID_ARG
 
 
 def test_shared_memory_executor_matches_oracle():
