@@ -41,6 +41,8 @@ def _bind(lib):
     i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
     lib.oracle_rcm.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i64p]
     lib.oracle_rcm.restype = ctypes.c_int
+    lib.oracle_rcm_ex.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i64p, ctypes.c_int]
+    lib.oracle_rcm_ex.restype = ctypes.c_int
     lib.oracle_bandwidth_profile.argtypes = [ctypes.c_int32, i32p, i32p, i32p,
                                              ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     lib.oracle_bandwidth_profile.restype = ctypes.c_int
@@ -77,13 +79,15 @@ def _arrays(rowptr, colidx):
     return rp, ci
 
 
-def rcm(n, rowptr, colidx, lib=None, with_stats=False):
-    """RCM permutation perm (new -> old) of the symmetric pattern; raises on a bad input."""
+def rcm(n, rowptr, colidx, lib=None, with_stats=False, row_order=0):
+    """RCM permutation perm (new -> old) of the symmetric pattern; raises on a bad input.
+    row_order=1: the sort-free variant (children numbered in stored row order)."""
     lib = lib or load()
     rp, ci = _arrays(rowptr, colidx)
     perm = np.empty(max(n, 1), dtype=np.int32)
     stats = np.zeros(8, dtype=np.int64)
-    rc = lib.oracle_rcm(int(n), rp, ci, perm, stats)
+    rc = lib.oracle_rcm_ex(int(n), rp, ci, perm, stats, int(row_order)) if row_order else \
+        lib.oracle_rcm(int(n), rp, ci, perm, stats)
     if rc != 0:
         raise ValueError(f"oracle_rcm: {STATUS.get(rc, rc)}")
     perm = perm[:n]

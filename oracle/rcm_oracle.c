@@ -20,6 +20,10 @@
  *     (Alg. 1 last line, Alg. 3 "return R in the reverse order").
  * Output: perm[k] = original vertex placed at new position k, so (P A P^T)_{ij} = A_{perm[i],perm[j]}.
  *
+ * oracle_rcm_ex(..., row_order = 1) is the sort-free variant of the paper's conclusion (no sort of
+ * a level beyond its parent order): the same steps, but each vertex's unnumbered neighbours are
+ * numbered in the order its row stores them instead of by (degree, id).
+ *
  * All arithmetic is integer. Functions are reentrant (no globals), so callers may run one graph
  * per thread.
  */
@@ -173,12 +177,14 @@ static int cmp_key(const void *pa, const void *pb)
  * Alg. 1 (Cuthill-McKee labelling) from root, labels starting at nv:
  *   v_1 <- root; for i = 1, 2, ...: find the unnumbered neighbours of v_i and number them in
  *   increasing order of degree (ties by lowest id).
+ * With by_degree = 0 (the sort-free variant the paper's conclusion proposes: the level is not
+ * sorted beyond its parent order) the neighbours are numbered in the order the row stores them.
  * label[] is -1 for unnumbered vertices. seq[] receives the vertices in label order from index nv.
  * Returns the new nv.
  */
 static int32_t cuthill_mckee(const int32_t *rowptr, const int32_t *colidx, const int32_t *deg,
                              int32_t root, int32_t nv, int32_t *label, int32_t *seq,
-                             int32_t *scratch, uint64_t *keys)
+                             int32_t *scratch, uint64_t *keys, int by_degree)
 {
     int32_t head = nv;
     label[root] = nv;
@@ -193,7 +199,9 @@ static int32_t cuthill_mckee(const int32_t *rowptr, const int32_t *colidx, const
                 scratch[found++] = w;
             }
         }
-        if (found <= 32) {
+        if (!by_degree) {
+            /* stored order: nothing to sort */
+        } else if (found <= 32) {
             sort_by_degree(scratch, found, deg);
         } else {
             for (int32_t i = 0; i < found; ++i)
@@ -215,7 +223,8 @@ static int32_t cuthill_mckee(const int32_t *rowptr, const int32_t *colidx, const
  *   [2] sum over components of ecc(root)+1 (levels of the labelled traversals),
  *   [3] largest ecc(root), [4] vertices of degree zero.
  */
-int oracle_rcm(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t *perm, int64_t *stats)
+int oracle_rcm_ex(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t *perm, int64_t *stats,
+                  int row_order)
 {
     int rc = oracle_check_csr(n, rowptr, colidx);
     if (rc) return rc;
@@ -245,7 +254,7 @@ int oracle_rcm(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t 
         int32_t r0 = start_order[cursor];
         int32_t sweeps, ecc;
         int32_t root = pseudo_peripheral(rowptr, colidx, deg, r0, lvl, queue, &sweeps, &ecc);
-        nv = cuthill_mckee(rowptr, colidx, deg, root, nv, label, seq, scratch, keys);
+        nv = cuthill_mckee(rowptr, colidx, deg, root, nv, label, seq, scratch, keys, row_order == 0);
         if (stats) {
             stats[0] += 1;
             stats[1] += sweeps;
@@ -259,6 +268,12 @@ int oracle_rcm(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t 
 done:
     free(deg); free(label); free(lvl); free(queue); free(seq); free(scratch); free(keys); free(start_order);
     return rc;
+}
+
+/* The ordering of Sec. II-A / III: children in (degree, id) order. */
+int oracle_rcm(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t *perm, int64_t *stats)
+{
+    return oracle_rcm_ex(n, rowptr, colidx, perm, stats, 0);
 }
 
 /*
@@ -306,7 +321,7 @@ int32_t oracle_cm_from_root(int32_t n, const int32_t *rowptr, const int32_t *col
     if (deg && seq && scratch && keys) {
         oracle_degrees(n, rowptr, colidx, deg);
         for (int32_t v = 0; v < n; ++v) label[v] = -1;
-        count = cuthill_mckee(rowptr, colidx, deg, root, 0, label, seq, scratch, keys);
+        count = cuthill_mckee(rowptr, colidx, deg, root, 0, label, seq, scratch, keys, 1);
     }
     free(deg); free(seq); free(scratch); free(keys);
     return count;

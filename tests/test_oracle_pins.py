@@ -154,10 +154,11 @@ def enumerate_cm_sequences(adj, deg, comp_roots, limit=3):
     return sols
 
 
-def alg3_level_synchronous(g, deg, root, nv0, R):
+def alg3_level_synchronous(g, deg, root, nv0, R, stored_order=False):
     """Alg. 3 restated with dense numpy vectors: SpMSpV over (select2nd, min) gives each discovered
     vertex the smallest label among its frontier neighbours; SELECT keeps unlabelled vertices;
-    SORTPERM orders them by (parent label, degree, id); labels continue from nv."""
+    SORTPERM orders them by (parent label, degree, id); labels continue from nv.
+    stored_order=True: the sort-free variant, (parent label, position in the parent's row)."""
     rp, ci = g.rowptr.astype(np.int64), g.colidx.astype(np.int64)
     R[root] = nv0
     nv = nv0 + 1
@@ -169,13 +170,19 @@ def alg3_level_synchronous(g, deg, root, nv0, R):
         w = ci[starts + offs]
         lab = np.repeat(R[cur], lens)
         sel = R[w] == -1                       # SELECT(R = -1)
-        w, lab = w[sel], lab[sel]
+        w, lab, offs = w[sel], lab[sel], offs[sel]
         if len(w) == 0:
             break
         parent = np.full(g.n, np.iinfo(np.int64).max)
         np.minimum.at(parent, w, lab)          # (select2nd, min)
         nxt = np.unique(w)
-        order = np.lexsort((nxt, deg[nxt], parent[nxt]))   # SORTPERM by (parent, degree, id)
+        if stored_order:
+            at = np.full(g.n, np.iinfo(np.int64).max)
+            mine = lab == parent[w]            # the entry of w in its parent's row
+            np.minimum.at(at, w[mine], offs[mine])
+            order = np.lexsort((at[nxt], parent[nxt]))
+        else:
+            order = np.lexsort((nxt, deg[nxt], parent[nxt]))   # SORTPERM by (parent, degree, id)
         nxt = nxt[order]
         R[nxt] = nv + np.arange(len(nxt))
         nv += len(nxt)
@@ -380,6 +387,52 @@ def test_alg3_level_form_equals_queue_form():
         assert np.array_equal(perm, rcm_of(g))
 
 
+def test_sort_free_variant_level_form_equals_queue_form():
+    """The sort-free variant (children in stored row order) against the level form with the key
+    (parent label, position in the parent's row)."""
+    for g in small_graphs(120, 400, 31) + [synth.c1_grid2d(), synth.c3_mesh(3000), synth.knn_mesh(2000, 3, 5)]:
+        deg = oracle.degrees(g.n, g.rowptr, g.colidx).astype(np.int64)
+        R = np.full(g.n, -1, dtype=np.int64)
+        nv = 0
+        for r0 in np.lexsort((np.arange(g.n), deg)):
+            if R[r0] != -1:
+                continue
+            root, _, _ = alg4_level_synchronous(g, deg, int(r0))
+            nv = alg3_level_synchronous(g, deg, root, nv, R, stored_order=True)
+        perm = np.empty(g.n, dtype=np.int64)
+        perm[g.n - 1 - R] = np.arange(g.n)
+        assert np.array_equal(perm, oracle.rcm(g.n, g.rowptr, g.colidx, row_order=1))
+
+
+def _rows_sorted_by_degree(g):
+    deg = oracle.degrees(g.n, g.rowptr, g.colidx).astype(np.int64)
+    ci = g.colidx.copy()
+    for v in range(g.n):
+        a, b = g.rowptr[v], g.rowptr[v + 1]
+        row = ci[a:b]
+        ci[a:b] = row[np.lexsort((row, deg[row]))]
+    return synth.Csr(g.n, g.rowptr, ci)
+
+
+def test_sort_free_variant_is_the_ordering_when_rows_are_stored_sorted():
+    """With every row stored in (degree, id) order the variant coincides with the ordering itself,
+    and the ordering does not depend on how rows are stored; on a star whose leaves are stored
+    in reverse id order it numbers the leaves in that stored order."""
+    for g in small_graphs(60, 300, 32) + [synth.c3_mesh(2000)]:
+        gs = _rows_sorted_by_degree(g)
+        exact = oracle.rcm(g.n, g.rowptr, g.colidx)
+        assert np.array_equal(oracle.rcm(gs.n, gs.rowptr, gs.colidx), exact)
+        assert np.array_equal(oracle.rcm(gs.n, gs.rowptr, gs.colidx, row_order=1), exact)
+    # star: centre 0, leaves 1..5 stored as 5, 4, 3, 2, 1 in the centre's row
+    rp = np.array([0, 5, 6, 7, 8, 9, 10], np.int32)
+    ci = np.array([5, 4, 3, 2, 1, 0, 0, 0, 0, 0], np.int32)
+    # start = leaf 1 (degree 1, lowest id); its sweep ends at leaf 2 (min (degree, id) of the last
+    # level), which the second sweep does not beat: root 2, then the centre, then the other
+    # leaves in the centre's stored order 5, 4, 3, 1; reversed.
+    assert list(oracle.rcm(6, rp, ci, row_order=1)) == [1, 3, 4, 5, 0, 2]
+    assert list(oracle.rcm(6, rp, ci)) == [5, 4, 3, 1, 0, 2]
+
+
 def test_alg4_level_form_matches_alg2():
     for g in small_graphs(120, 300, 25, connected=True) + [synth.grid((9, 14), seed=3)]:
         deg = oracle.degrees(g.n, g.rowptr, g.colidx).astype(np.int64)
@@ -522,6 +575,7 @@ MUTANTS = {
     "last_level_off_by_one": ("*last = i;\n    return tail;", "*last = i > 0 ? i - 1 : 0;\n    return tail;"),
     "one_sweep_only": ("    while (ecc_r > nlvl) {", "    while (0) {"),
     "bandwidth_f_starts_at_zero": ("int32_t v = perm[i], f = i;", "int32_t v = perm[i], f = 0;"),
+    "sort_free_still_sorts": ("        if (!by_degree) {", "        if (0) {"),
     "start_at_highest_degree": ("while (label[start_order[cursor]] >= 0) cursor++;\n        int32_t r0 = start_order[cursor];",
                                 "int32_t r0 = -1;\n        for (int32_t c = n - 1; c >= 0; --c) if (label[start_order[c]] < 0) { r0 = start_order[c]; break; }"),
 }
@@ -549,6 +603,10 @@ def _pins_with(lib):
             p = oracle.rcm(g.n, g.rowptr, g.colidx, lib=lib)
             if len(sols) != 1 or list(p[::-1]) != sols[0]:
                 return False
+        rp = np.array([0, 5, 6, 7, 8, 9, 10], np.int32)          # the stored-order star above
+        ci = np.array([5, 4, 3, 2, 1, 0, 0, 0, 0, 0], np.int32)
+        if list(oracle.rcm(6, rp, ci, lib=lib, row_order=1)) != [1, 3, 4, 5, 0, 2]:
+            return False
         for i in range(10):
             g = synth.random_graph(40, 70, [30, i])
             gd = synth.csr_from_edges(40, *_edges(g), diagonal=np.arange(0, 40, 3))
