@@ -45,6 +45,7 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-served", action="store_true")
+    p.add_argument("--no-sort-free", action="store_true", help="skip the sort-free variant's line")
     p.add_argument("--batch-graphs", type=int, default=10_000)
     p.add_argument("--serve-requests", type=int, default=4000)
     p.add_argument("--serve-pool", type=int, default=256)
@@ -87,6 +88,12 @@ def kernel_sources_hash() -> str:
             h.update(f.encode())
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def ctypes_copy(src, dst):
+    """Copies every field of one ctypes structure into another of the same type."""
+    for f, _ in src._fields_:
+        setattr(dst, f, getattr(src, f))
 
 
 def parse_launch(text: str) -> dict:
@@ -450,6 +457,32 @@ def main():
     qual = quality.report(rp, ci, perm)
     bw, prof = qual["bandwidth_rcm"], qual["profile_rcm"]
 
+    # the sort-free variant (opt-in, changes the result): time per ordering and what it costs in
+    # quality, outside the timed region of the main metric
+    sort_free = None
+    if not args.no_sort_free:
+        sf = rcm.rcm_options()
+        ctypes_copy(opts, sf)
+        sf.row_order = 1
+        perm_sf = torch.empty_like(perm)
+        rcm.check(rcm.rcm_order_ex(n, rp, ci, perm_sf, sf, None, stream), "rcm_order_ex")
+        ts = []
+        for i in range(max(3, min(args.steps, 10))):
+            flush.fill_(i)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rcm.check(rcm.rcm_order_ex(n, rp, ci, perm_sf, sf, None, stream), "rcm_order_ex")
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        rcm.check(rcm.rcm_stream_status(stream), "rcm_order_ex")
+        qsf = quality.report(rp, ci, perm_sf)
+        sort_free = {"variant": "children numbered in stored row order (no (degree, id) row sort); changes the result",
+                     "ms_per_ordering": statistics.median(ts), "exact_ms_per_ordering": statistics.median(step_ms),
+                     "bandwidth": qsf["bandwidth_rcm"], "profile": qsf["profile_rcm"], "spmv_ms": qsf["spmv_ms_rcm"],
+                     "bandwidth_exact": bw, "profile_exact": prof, "spmv_ms_exact": qual["spmv_ms_rcm"]}
+
     # roofline of the dominant kernel: the persistent traversal kernel
     peak, peak_kind = load_peaks()
     labelled = 1 if stats["traversals"] == stats["sweeps"] else stats["traversals"] - stats["sweeps"] + 1
@@ -509,7 +542,7 @@ def main():
             # per step: k_degree_validate, k_sort_rows_small, k_sort_rows_big, k_rcm_single, k_latch
             "gpu_launches": 5 * args.steps, "clocks": clocks,
             "stats": dict(stats, prep_ms=statistics.mean(prep_ms), traverse_ms=trav),
-            "quality": dict(qual, bandwidth=bw, profile=prof),
+            "quality": dict(qual, bandwidth=bw, profile=prof), "sort_free": sort_free,
             "batched": batched, "served": served,
         }
         print(json.dumps(line), flush=True)

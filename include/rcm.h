@@ -63,8 +63,8 @@ typedef enum {
 /* Human-readable name of a status code (static storage). */
 const char *rcm_status_string(rcm_status s);
 
-/* Tuning knobs. None of them changes the result: every setting yields the same permutation.
-   Zero-initialise and set what you need; 0 means "library default" in every field. */
+/* Tuning knobs. None of them changes the result, except row_order: every other setting yields the
+   same permutation. Zero-initialise and set what you need; 0 means "library default" in every field. */
 typedef struct {
     int32_t narrow_threshold;  /* frontier size below which a single CTA runs the levels; -1 = never */
     int32_t grid_blocks;       /* CTAs of the persistent grid (<= co-resident limit); 0 = one per SM */
@@ -98,6 +98,12 @@ typedef struct {
     int32_t debug_async_slots; /* test hook: slots of the asynchronous sweeps' work queue (0 = 2n).
                                   A queue that runs full makes the sweep, and every later one of
                                   the call, run level by level instead: same result, slower.        */
+    int32_t row_order;         /* 0 = the ordering above: each level by (parent label, degree, id).
+                                  1 = the sort-free variant the paper's conclusion names (no sort
+                                  beyond the parent order): a vertex's children are numbered in the
+                                  order its row stores them. CHANGES THE RESULT (usually a somewhat
+                                  larger bandwidth and profile); saves the degree gather of the
+                                  row sort.                                                         */
 } rcm_options;
 
 /* Statistics of one ordering (filled by rcm_order_ex when requested). */
@@ -166,12 +172,14 @@ rcm_status rcm_order_host(int32_t n, const int32_t *rowptr, const int32_t *colid
 rcm_status rcm_order_batch(int32_t G, int64_t n_total, const int64_t *goff, const int32_t *rowptr,
                            const int32_t *colidx, int32_t *perm_out, rcm_stream_t stream);
 
-/* Tuning of the batched path (every value gives the same permutations; only speed differs). */
+/* Tuning of the batched path (apart from row_order, every value gives the same permutations;
+   only speed differs). */
 typedef struct {
     int32_t block_threads;   /* threads per CTA of the batched executor: 128, 256 or 512; 0 = 256   */
     int32_t row_sort_split;  /* rows with at most this many stored entries are sorted by one thread,
                                 longer rows by a whole CTA: 4..32; 0 = 32                          */
-    int32_t reserved[6];
+    int32_t row_order;       /* as rcm_options.row_order: 1 = sort-free variant (changes the result) */
+    int32_t reserved[5];
 } rcm_batch_options;
 
 /* rcm_order_batch with tuning options (opts may be NULL = defaults). RCM_ERR_INVALID_ARG for

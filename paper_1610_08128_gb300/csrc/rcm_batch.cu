@@ -173,6 +173,8 @@ rcm_status batch_tuning(const rcm_batch_options* o, BatchTuning* out) {
     if (o) {
         if (o->block_threads) t.threads = o->block_threads;
         if (o->row_sort_split) t.small_max = o->row_sort_split;
+        if (o->row_order != 0 && o->row_order != 1) return RCM_ERR_INVALID_ARG;
+        t.by_degree = o->row_order ? 0 : 1;
     }
     if (batch_index(t.threads) < 0 || t.small_max < 4 || t.small_max > kSmallRowMax) return RCM_ERR_INVALID_ARG;
     *out = t;
@@ -207,9 +209,10 @@ cudaError_t enqueue_batch(int G, long long n_total, int nnz, const long long* go
     const int big_grid = (int)std::max<long long>(1, std::min<long long>(2LL * di.sms, nnz / (t.small_max + 1)));
     if (G > 1) k_batch_validate<<<pgrid, pb, 0, s>>>(G, (int)n_total, goff, rowptr, colidx, ctl);
     k_degree_validate<<<pgrid, pb, 0, s>>>((int)n_total, nnz, rowptr, colidx, deg, claim, vis, big, ctl, t.small_max);
-    k_sort_rows_small<<<pgrid, pb, 0, s>>>((int)n_total, rowptr, colidx, deg, adj, ell, ctl, t.small_max);
+    k_sort_rows_small<<<pgrid, pb, 0, s>>>((int)n_total, rowptr, colidx, deg, adj, ell, ctl, t.small_max,
+                                           t.by_degree);
     k_sort_rows_big<<<big_grid, 1024, sizeof(unsigned long long) * kBigRowSmem, s>>>(
-        (int)n_total, rowptr, colidx, deg, adj, ell, big, ctl, (unsigned long long*)pool4);
+        (int)n_total, rowptr, colidx, deg, adj, ell, big, ctl, (unsigned long long*)pool4, t.by_degree);
     BatchArgs b;
     b.G = G;
     b.goff = goff;

@@ -45,10 +45,12 @@ BatchLayout batch_layout(long long N, long long nnz, long long G = 1);
 std::vector<int> batch_order(const std::vector<long long>& goff);
 
 // Tuning of the batched path: CTA width of the executor (128, 256, 512) and the row length up to
-// which one thread sorts a row (4..kSmallRowMax). Every value gives the same result.
+// which one thread sorts a row (4..kSmallRowMax); every value gives the same result. by_degree = 0
+// selects the sort-free variant (rows in stored order), which changes the result.
 struct BatchTuning {
     int threads = 256;
     int small_max = 32;
+    int by_degree = 1;
 };
 // RCM_OK and the tuning for the options, or RCM_ERR_INVALID_ARG.
 rcm_status batch_tuning(const rcm_batch_options* o, BatchTuning* out);

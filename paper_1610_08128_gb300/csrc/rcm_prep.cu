@@ -4,7 +4,8 @@
 //    Alg. 3 and Alg. 4 take as input) plus the structural checks of the pattern.
 //  * k_sort_rows_small / k_sort_rows_big: every row with the diagonal dropped and the neighbours in
 //    increasing (degree, id), stored as a padded 32-byte row per vertex (7 neighbours + degree) and,
-//    for rows of degree > 7, as a full sorted copy. Sorting each adjacency row once replaces the
+//    for rows of degree > 7, as a full sorted copy. (by_degree = 0: stored order instead, for the
+//    sort-free variant.) Sorting each adjacency row once replaces the
 //    per-level SortPerm of Sec. IV-B: when a frontier vertex scans its sorted row, the children it
 //    owns come out already in (degree, id) order, so the new level is ordered by (parent label,
 //    degree, id) by a prefix sum over parents alone.
@@ -53,10 +54,10 @@ __global__ void k_degree_validate(int n, int nnz, const int* __restrict__ rowptr
 // Rows of at most kSmallRowMax stored entries: one thread per row (sort_small_row).
 __global__ void k_sort_rows_small(int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
                                   const int* __restrict__ deg, int* __restrict__ adj, int4* __restrict__ ell,
-                                  const Ctl* ctl, int small_max) {
+                                  const Ctl* ctl, int small_max, int by_degree) {
     if (ctl->status & kErrBadCsr) return;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-        if (rowptr[v + 1] - rowptr[v] <= small_max) sort_small_row(v, rowptr, colidx, deg, adj, ell);
+        if (rowptr[v + 1] - rowptr[v] <= small_max) sort_small_row(v, rowptr, colidx, deg, adj, ell, by_degree);
 }
 
 // Rows longer than the per-thread sorter: one CTA per row, bitonic sort in shared memory for rows
@@ -65,7 +66,7 @@ __global__ void k_sort_rows_small(int n, const int* __restrict__ rowptr, const i
 __global__ void k_sort_rows_big(int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
                                 const int* __restrict__ deg, int* __restrict__ adj, int4* __restrict__ ell,
                                 const int* __restrict__ bigrows, const Ctl* ctl,
-                                unsigned long long* __restrict__ scratch) {
+                                unsigned long long* __restrict__ scratch, int by_degree) {
     extern __shared__ unsigned long long s_keys[];
     __shared__ int s_m;
     if (ctl->status & kErrBadCsr) return;
@@ -83,7 +84,7 @@ __global__ void k_sort_rows_big(int n, const int* __restrict__ rowptr, const int
         __syncthreads();
         for (int k = a + threadIdx.x; k < b; k += blockDim.x) {
             const int w = colidx[k];
-            if (w != v) s[atomicAdd(&s_m, 1)] = pack_key(__ldg(deg + w), w);
+            if (w != v) s[atomicAdd(&s_m, 1)] = row_key(deg, w, k - a, by_degree);
         }
         __syncthreads();
         for (int i = m + threadIdx.x; i < P; i += blockDim.x) s[i] = kKeyMax;
@@ -112,7 +113,7 @@ __global__ void k_sort_rows_big(int n, const int* __restrict__ rowptr, const int
         __syncthreads();
         for (int k = a + threadIdx.x; k < b; k += blockDim.x) {
             const int w = colidx[k];
-            if (w != v) scratch[atomicAdd(&s_m, 1)] = pack_key(__ldg(deg + w), w);
+            if (w != v) scratch[atomicAdd(&s_m, 1)] = row_key(deg, w, k - a, by_degree);
         }
         __syncthreads();
         for (int i = m + threadIdx.x; i < P; i += blockDim.x) scratch[i] = kKeyMax;

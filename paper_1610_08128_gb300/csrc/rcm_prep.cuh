@@ -51,18 +51,24 @@ __device__ __forceinline__ bool row_degree(int n, int nnz, const int* __restrict
     return ok;
 }
 
+// Sort key of neighbour w, stored at position p of its row: (degree, id), or with by_degree = 0
+// (the sort-free variant) its position, which keeps the stored order.
+__device__ __forceinline__ unsigned long long row_key(const int* __restrict__ deg, int w, int p, int by_degree) {
+    return pack_key(by_degree ? __ldg(deg + w) : p, w);
+}
+
 // Sorted row of a vertex with at most kSmallRowMax stored entries, by one thread: the padded row
 // and, for degree > 7, the full sorted row in adj (same offsets as the input row).
 __device__ __forceinline__ void sort_small_row(int v, const int* __restrict__ rowptr, const int* __restrict__ colidx,
                                                const int* __restrict__ deg, int* __restrict__ adj,
-                                               int4* __restrict__ ell) {
+                                               int4* __restrict__ ell, int by_degree) {
     const int a = rowptr[v], b = rowptr[v + 1];
     unsigned long long key[kSmallRowMax];
     int m = 0;
     for (int k = a; k < b; ++k) {
         const int w = colidx[k];
         if (w == v) continue;
-        const unsigned long long x = pack_key(__ldg(deg + w), w);
+        const unsigned long long x = row_key(deg, w, k - a, by_degree);
         int j = m++;
         while (j > 0 && key[j - 1] > x) {
             key[j] = key[j - 1];
@@ -79,37 +85,6 @@ __device__ __forceinline__ void sort_small_row(int v, const int* __restrict__ ro
         for (int i = 0; i < m; ++i) adj[a + i] = (int)(unsigned)(key[i] & 0xffffffffu);
 }
 
-// Sorted row of one long row by the whole CTA: keys gathered into `s` (kBigRowSmem keys of shared
-// memory, or global scratch of next_pow2(degree) keys), bitonic-sorted, written to adj and ell.
-// s_m: one shared int.
-__device__ __forceinline__ void sort_big_row_cta(int v, const int* __restrict__ rowptr,
-                                                 const int* __restrict__ colidx, const int* __restrict__ deg,
-                                                 int* __restrict__ adj, int4* __restrict__ ell,
-                                                 unsigned long long* s, int* s_m) {
-    const int a = rowptr[v], b = rowptr[v + 1];
-    const int m = deg[v];
-    int P = 1;
-    while (P < m) P <<= 1;
-    if (threadIdx.x == 0) *s_m = 0;
-    __syncthreads();
-    for (int k = a + threadIdx.x; k < b; k += blockDim.x) {
-        const int w = colidx[k];
-        if (w != v) s[atomicAdd(s_m, 1)] = pack_key(__ldg(deg + w), w);
-    }
-    __syncthreads();
-    for (int i = m + threadIdx.x; i < P; i += blockDim.x) s[i] = kKeyMax;
-    __syncthreads();
-    bitonic_sort_cta(s, P);
-    for (int i = threadIdx.x; i < m; i += blockDim.x) adj[a + i] = (int)(unsigned)(s[i] & 0xffffffffu);
-    if (threadIdx.x == 0) {
-        int r[8];
-        for (int i = 0; i < 7; ++i) r[i] = i < m ? (int)(unsigned)(s[i] & 0xffffffffu) : -1;
-        r[7] = m;
-        store_ell(ell, v, r);
-    }
-    __syncthreads();
-}
-
 // nnz: the stored-entry count the caller sized its buffers for; rowptr[n] must equal it, and no
 // row is read beyond it. adist (may be null): the asynchronous sweeps' per-vertex words, cleared.
 __global__ void k_degree_validate(int n, int nnz, const int* __restrict__ rowptr, const int* __restrict__ colidx,
@@ -119,14 +94,15 @@ __global__ void k_degree_validate(int n, int nnz, const int* __restrict__ rowptr
 
 // small_max (<= kSmallRowMax): rows with at most this many stored entries are sorted here, one
 // thread per row; k_degree_validate lists the longer ones for k_sort_rows_big with the same value.
+// by_degree: 1 = rows in (degree, id) order; 0 = stored order (the sort-free variant).
 __global__ void k_sort_rows_small(int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
                                   const int* __restrict__ deg, int* __restrict__ adj, int4* __restrict__ ell,
-                                  const Ctl* ctl, int small_max);
+                                  const Ctl* ctl, int small_max, int by_degree = 1);
 
 __global__ void k_sort_rows_big(int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
                                 const int* __restrict__ deg, int* __restrict__ adj, int4* __restrict__ ell,
                                 const int* __restrict__ bigrows, const Ctl* ctl,
-                                unsigned long long* __restrict__ scratch);
+                                unsigned long long* __restrict__ scratch, int by_degree = 1);
 
 __global__ void k_bw_scatter(int n, const int* __restrict__ perm, int* __restrict__ pos, int* __restrict__ err);
 

@@ -179,6 +179,7 @@ rcm_status single_launch(int n, const rcm_options& o, SingleLaunch* out) {
         if (g_small_attr != cudaSuccess) return RCM_ERR_CUDA;
         single_blocks_per_sm(512);  // sets up the preprocessing kernels' attributes
         sl.small = true;
+        sl.by_degree = o.row_order ? 0 : 1;
         sl.threads = t;
         sl.blocks = 1;
         sl.fused = o.fused_sweeps >= 0 ? 1 : 0;
@@ -219,6 +220,7 @@ rcm_status single_launch(int n, const rcm_options& o, SingleLaunch* out) {
     sl.profile = o.profile_phases ? 1 : 0;
     sl.stall = o.debug_stall_barrier ? 1 : 0;
     sl.async_slots = o.debug_async_slots;
+    sl.by_degree = o.row_order ? 0 : 1;
     *out = sl;
     return RCM_OK;
 }
@@ -246,11 +248,12 @@ cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* c
         const int pgrid = (int)std::min<long long>((n + pb - 1) / pb, (long long)di.sms * 16);
         k_degree_validate<<<std::max(pgrid, 1), pb, 0, s>>>(n, (int)nnz, rowptr, colidx, deg, claim, vis, bigrows, ctl,
                                                            kSmallRowMax, adist);
-        k_sort_rows_small<<<std::max(pgrid, 1), pb, 0, s>>>(n, rowptr, colidx, deg, adj, ell, ctl, kSmallRowMax);
+        k_sort_rows_small<<<std::max(pgrid, 1), pb, 0, s>>>(n, rowptr, colidx, deg, adj, ell, ctl, kSmallRowMax,
+                                                           sl.by_degree);
         // rows longer than kSmallRowMax entries number at most nnz / (kSmallRowMax + 1)
         const int big_grid = (int)std::max<long long>(1, std::min<long long>(2LL * di.sms, nnz / (kSmallRowMax + 1)));
         k_sort_rows_big<<<big_grid, 1024, sizeof(unsigned long long) * kBigRowSmem, s>>>(
-            n, rowptr, colidx, deg, adj, ell, bigrows, ctl, (unsigned long long*)pool4);
+            n, rowptr, colidx, deg, adj, ell, bigrows, ctl, (unsigned long long*)pool4, sl.by_degree);
         e = cudaGetLastError();
         if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
     }

@@ -36,6 +36,7 @@ struct SingleLaunch {
     int stall = 0;
     bool async = false;          // levels-only sweeps through the asynchronous work queue
     int async_slots = 0;         // its capacity (0 = 2n)
+    int by_degree = 1;           // rows in (degree, id) order; 0 = stored order (sort-free variant)
 };
 
 // Derives the launch shape from options for a graph of n vertices; RCM_ERR_INVALID_ARG for

@@ -42,12 +42,13 @@ class rcm_options(ctypes.Structure):
         ("executor", ctypes.c_int32),
         ("async_sweeps", ctypes.c_int32),
         ("debug_async_slots", ctypes.c_int32),
+        ("row_order", ctypes.c_int32),
     ]
 
 
 class rcm_batch_options(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int32), ("row_sort_split", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("row_order", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class rcm_server_options(ctypes.Structure):

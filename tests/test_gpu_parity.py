@@ -196,6 +196,38 @@ def test_async_sweeps_on_large_graphs():
     assert rcm.rcm_order_ex(g.n, rp, ci, pm, o, None) == rcm.RCM_ERR_INVALID_ARG
 
 
+def test_sort_free_variant_matches_the_oracle_variant():
+    """rcm_options.row_order = 1 (children in stored row order) equals the oracle's sort-free
+    variant on every executor: the persistent grid, the shared-memory CTA and the batched engine,
+    including rows long enough for the whole-CTA sorter and rows stored in reverse."""
+    rcm = rcm_mod()
+    star = synth.csr_from_edges(20001, np.zeros(20000, np.int64), np.arange(1, 20001))
+    rev = synth.Csr(star.n, star.rowptr, np.concatenate([star.colidx[:20000][::-1], star.colidx[20000:]]))
+    graphs = [synth.c1_grid2d(), synth.grid((30, 20, 9), seed=81), synth.c3_mesh(20000), synth.knn_mesh(5000, 3, 82),
+              synth.random_tree(3000, 83), rev, synth.random_graph(2000, 900, 84)] + small_graphs(40, 300, 85)
+    for g in graphs:
+        want = oracle.rcm(g.n, g.rowptr, g.colidx, row_order=1)
+        assert np.array_equal(gpu_perm(g, {"row_order": 1}), want)
+        assert np.array_equal(gpu_perm(g, {"row_order": 1, "executor": 1}), want)
+        if g.n <= 4608:
+            assert np.array_equal(gpu_perm(g, {"row_order": 1, "executor": 2}), want)
+    batch = [g for g in graphs if g.n <= 30000]
+    b = synth.concat(batch)
+    goff = torch.from_numpy(b.goff).cuda()
+    rp = torch.from_numpy(b.rowptr).cuda()
+    ci = torch.from_numpy(b.colidx).cuda()
+    o = rcm.rcm_batch_options()
+    o.row_order = 1
+    perm = torch.empty(b.n, dtype=torch.int32, device="cuda")
+    rcm.check(rcm.rcm_order_batch_ex(len(batch), b.n, goff, rp, ci, perm, o), "batch_ex")
+    rcm.check(rcm.rcm_stream_status(), "batch_ex")
+    host = perm.cpu().numpy()
+    for gi, g in enumerate(batch):
+        assert np.array_equal(host[b.goff[gi]:b.goff[gi + 1]], oracle.rcm(g.n, g.rowptr, g.colidx, row_order=1))
+    o.row_order = 2
+    assert rcm.rcm_order_batch_ex(len(batch), b.n, goff, rp, ci, perm, o) == rcm.RCM_ERR_INVALID_ARG
+
+
 def test_shared_memory_executor_matches_oracle():
     """One CTA with the graph's claims, stamps and padded rows in shared memory (graphs of at most
     4,608 vertices): the same orders as the oracle and the persistent grid, on grids, meshes with
