@@ -20,7 +20,7 @@
  *             non-decreasing), colidx[rowptr[n]] with 0 <= colidx < n. Values are not passed
  *             (Sec. III-A: only where the nonzeros are matters). Diagonal entries are allowed and
  *             ignored. Column order inside a row is free. Duplicate entries are not allowed.
- *             Symmetry is a precondition and is not checked.
+ *             Symmetry is a precondition and is not checked (rcm_validate checks it).
  *   Output    perm[k] = original vertex placed at new position k (new -> old), so that
  *             (P A P^T)_{ij} = A_{perm[i], perm[j]}.
  *   Memory    Pointers documented as "device" must be device-accessible memory of the current
@@ -311,6 +311,33 @@ rcm_status rcm_stream_status(rcm_stream_t stream);
 
 /* Workspace bytes rcm_order allocates for a pattern of n vertices and nnz stored entries. */
 size_t rcm_workspace_bytes(int32_t n, int64_t nnz);
+
+/* What rcm_validate found. Counts are of stored entries unless named otherwise. */
+typedef struct {
+    int64_t bad_rows;       /* rows v with rowptr[v] < 0, rowptr[v+1] < rowptr[v] or rowptr[v+1] > rowptr[n];
+                               rowptr[0] != 0 counts as one more                                      */
+    int64_t bad_columns;    /* entries with a column outside [0, n)                                   */
+    int64_t duplicates;     /* entries equal to another entry of the same row (each extra copy once);
+                               -1 = not checked (rows or columns malformed)                           */
+    int64_t asymmetric;     /* off-diagonal entries (v, w) whose row w holds no v; -1 = not checked   */
+    int64_t diagonal;       /* diagonal entries (allowed; the ordering ignores them)                  */
+    int64_t max_row;        /* stored entries of the longest well-formed row                          */
+    int64_t first_bad_row;  /* smallest row holding a fault counted above, -1 if none                 */
+    int64_t reserved;
+} rcm_validate_report;
+
+/*
+ * rcm_validate -- checks a pattern against the contract every ordering call assumes (file header):
+ * CSR structure, columns in range, no duplicate entries, and symmetry (the graph of A is
+ * undirected, Sec. II-A; the ordering calls take symmetry as a precondition and do not check it).
+ * rowptr, colidx: device, as for rcm_order. report: host, filled on RCM_OK and on RCM_ERR_BAD_CSR.
+ * Returns RCM_OK when the pattern meets the contract, RCM_ERR_BAD_CSR when it does not (report
+ * says why), RCM_ERR_INVALID_ARG for n < 0 or null pointers. Synchronous: waits for `stream`.
+ * A debugging aid, off the ordering path: it sorts a copy of every row (4 bytes per entry of
+ * workspace) and binary-searches each entry's partner row.
+ */
+rcm_status rcm_validate(int32_t n, const int32_t *rowptr, const int32_t *colidx, rcm_validate_report *report,
+                        rcm_stream_t stream);
 
 /*
  * rcm_bandwidth_profile -- bandwidth and profile of P A P^T (Sec. II-A): with pos = perm^-1 and

@@ -69,6 +69,14 @@ class rcm_stats(ctypes.Structure):
         return out
 
 
+class rcm_validate_report(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in (
+        "bad_rows", "bad_columns", "duplicates", "asymmetric", "diagonal", "max_row", "first_bad_row", "reserved")]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}
+
+
 class rcm_server_stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in (
         "submitted", "completed", "failed", "cancelled", "waiting", "running", "max_running", "arena_bytes",
@@ -110,6 +118,7 @@ def load():
         "rcm_stream_status": ([P], ctypes.c_int),
         "rcm_workspace_bytes": ([I32, I64], SZ),
         "rcm_bandwidth_profile": ([I32, P, P, P, ctypes.POINTER(I64), ctypes.POINTER(I64), P], ctypes.c_int),
+        "rcm_validate": ([I32, P, P, ctypes.POINTER(rcm_validate_report), P], ctypes.c_int),
         "rcm_request_bytes": ([I32, I64, I32, I32], SZ),
         "rcm_server_create": ([SZ, I32, ctypes.POINTER(P)], ctypes.c_int),
         "rcm_server_create_ex": ([SZ, I32, ctypes.POINTER(rcm_server_options), ctypes.POINTER(P)], ctypes.c_int),
@@ -239,6 +248,11 @@ def rcm_workspace_bytes(n, nnz) -> int:
     return int(load().rcm_workspace_bytes(int(n), int(nnz)))
 
 
+def rcm_validate(n, rowptr, colidx, report: rcm_validate_report, stream=None) -> int:
+    return load().rcm_validate(int(n), _ptr(rowptr, True, _i32()), _ptr(colidx, True, _i32()), ctypes.byref(report),
+                               _stream(stream))
+
+
 def rcm_bandwidth_profile(n, rowptr, colidx, perm, stream=None):
     """Returns (status, bandwidth, profile)."""
     bw, prof = ctypes.c_int64(0), ctypes.c_int64(0)
@@ -328,6 +342,16 @@ def order_batch(goff, rowptr, colidx, stream=None):
     check(rcm_order_batch(G, n_total, goff, rowptr, colidx, perm, stream), "rcm_order_batch")
     check(rcm_stream_status(stream), "rcm_order_batch")
     return perm
+
+
+def validate(rowptr, colidx, stream=None):
+    """(ok, report dict): the pattern checked against the library's contract (structure, columns,
+    duplicates, symmetry) by rcm_validate."""
+    rep = rcm_validate_report()
+    st = rcm_validate(rowptr.numel() - 1, rowptr, colidx, rep, stream)
+    if st not in (RCM_OK, RCM_ERR_BAD_CSR):
+        check(st, "rcm_validate")
+    return st == RCM_OK, rep.as_dict()
 
 
 def bandwidth_profile(rowptr, colidx, perm, stream=None):

@@ -88,7 +88,8 @@ def test_binding_structures_match_the_header(tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if not cc:
         pytest.skip("no host C compiler")
-    structs = [rcm.rcm_options, rcm.rcm_batch_options, rcm.rcm_server_options, rcm.rcm_stats, rcm.rcm_server_stats]
+    structs = [rcm.rcm_options, rcm.rcm_batch_options, rcm.rcm_server_options, rcm.rcm_stats, rcm.rcm_server_stats,
+               rcm.rcm_validate_report]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rcm.h"', "int main(void) {"]
     for st in structs:
         name = st.__name__
