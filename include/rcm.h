@@ -104,6 +104,19 @@ typedef struct {
                                   order its row stores them. CHANGES THE RESULT (usually a somewhat
                                   larger bandwidth and profile); saves the degree gather of the
                                   row sort.                                                         */
+    int32_t expand_mode;       /* expansion of the persistent grid's whole-grid levels; the result is
+                                  the same in every mode:
+                                  1 = top-down only: the frontier's atomicMin on its neighbours;
+                                  2 = bottom-up on every whole-grid level: each vertex not yet reached
+                                      scans its own row;
+                                  3 = chosen per level: bottom-up once the frontier is a large part
+                                      of the graph, top-down otherwise;
+                                  0 = automatic: 3 for patterns averaging at least 8 stored entries
+                                      per row (low-diameter graphs, whose frontiers grow wide), 1
+                                      otherwise.
+                                  Modes 2 and 3 need 512-thread CTAs and level-by-level sweeps
+                                  (else RCM_ERR_INVALID_ARG; 0 then means 1). Narrow levels and the
+                                  CTA executors are always top-down.                                */
 } rcm_options;
 
 /* Statistics of one ordering (filled by rcm_order_ex when requested). */

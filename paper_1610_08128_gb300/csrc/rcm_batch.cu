@@ -92,6 +92,12 @@ __global__ void __launch_bounds__(kThreads) k_rcm_batch(BatchArgs b) {
         a.cc_big = 0;
         a.fused = 1;
         a.limit_ns = 0;
+        a.fkey = nullptr;  // CTA engines: top-down, level by level
+        a.expand_mode = 1;
+        a.adist = nullptr;
+        a.aq = nullptr;
+        a.actl = nullptr;
+        a.aq_cap = 0;
         __syncthreads();
         e.init(a, &smem);
         e.sm_sort = s_sort;

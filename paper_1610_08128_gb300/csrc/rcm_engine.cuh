@@ -83,6 +83,9 @@ struct EngineArgs {
     int4* cc_tab;                // cc_cap entries: (start vertex, first label, size, root)
     int cc_cap;                  // most components ordered concurrently (else one by one)
     int cc_big;                  // components at least this large run on the whole grid
+    // bottom-up expansion (whole-grid executor only; fkey == null: top-down only)
+    unsigned long long* fkey;    // n words: a labelled frontier vertex's key, published for bottom-up claims
+    int expand_mode;             // 2 = bottom-up on every grid level, 1 = top-down, else per level by frontier size
     // asynchronous levels-only sweeps (whole-grid executor only; adist == null: level by level)
     unsigned long long* adist;   // n words: (~sweep stamp) << 32 | breadth-first distance
     unsigned long long* aq;      // work queue of aq_cap (distance << 32 | vertex) items
@@ -127,12 +130,14 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
 // memory, indexed from the graph's first vertex v0; otherwise they are global arrays indexed by
 // vertex id.
 // kAsync (whole-grid engine only): levels-only sweeps through the asynchronous work queue when
-// the arguments provide it. A separate instantiation, so the level-by-level kernels carry none of
-// its code or registers.
-template <bool kCtaOnly, bool kSmem = false, bool kAsync = false>
+// the arguments provide it. kBottomUp (whole-grid engine only): each whole-grid level may run
+// bottom-up, chosen per level. Separate instantiations, so the plain top-down kernels carry none
+// of their code or registers.
+template <bool kCtaOnly, bool kSmem = false, bool kAsync = false, bool kBottomUp = false>
 struct Engine {
     static_assert(kCtaOnly || !kSmem, "shared-memory state needs a CTA engine");
     static_assert(!kAsync || !kCtaOnly, "asynchronous sweeps need the whole grid");
+    static_assert(!kBottomUp || !kCtaOnly, "bottom-up levels need the whole grid");
     const EngineArgs* a;   // in shared memory (keeps the per-thread register footprint small)
     unsigned epoch;
     int sweep_id;
@@ -413,6 +418,79 @@ struct Engine {
             cnt += c;
         }
         accumulate(cnt, key);
+    }
+
+    // ---------------- bottom-up expansion (whole grid) ----------------
+    // Top-down, a level's frontier pushes to its neighbours. Bottom-up, every vertex not yet reached
+    // looks at its own neighbours instead. An unvisited vertex has no neighbour in a level below
+    // the current one (its neighbours there would have reached it), so "some neighbour visited" means
+    // "some neighbour in the current level", and the smallest frontier key among its neighbours is
+    // what the top-down atomicMin would leave in its claim. Both give the same levels and labels;
+    // bottom-up reads every vertex once per level and pays off only when the frontier is a large
+    // part of the graph.
+
+    // Whether whole-grid level work of frontier size F, with `seen` vertices already reached, runs
+    // bottom-up. Uniform over the grid (every CTA holds the same F and seen).
+    __device__ bool bottom_up(long long F, long long seen) const {
+        if constexpr (!kBottomUp) return false;
+        if (!a->fkey || a->expand_mode == 1) return false;
+        if (a->expand_mode == 2) return true;
+        return F * 16 >= a->n && F * 4 >= (long long)a->n - seen;
+    }
+
+    // Levels-only, bottom-up: every vertex not stamped s with a stamped neighbour is appended to
+    // nxt, unstamped (the caller stamps the new level after the exchange, so that this pass never
+    // sees it). Accumulates their count and the min (degree, id) over the frontier slice [lo, hi).
+    __device__ void expand_levels_bottom_up(int s, const int* cur, int lo, int hi, int* nxt, int* tail) {
+        const int T = blockDim.x, n = a->n;
+        unsigned long long key = kKeyMax;
+        for (int i = lo + (int)threadIdx.x; i < hi; i += T) {
+            const int u = ldcg(cur + i);
+            if (in_graph(u)) key = min(key, pack_key(__ldg(a->deg + u), u));
+        }
+        int cnt = 0;
+        const int stride = cta_count() * T;
+        for (int i0 = cta_rank() * T; i0 < n; i0 += stride) {
+            const int i = i0 + (int)threadIdx.x;
+            const int w = a->v0 + i;
+            bool found = false;
+            if (i < n && ldcg(vis_p(w)) != s) {
+                int r[8];
+                load_row(w, r);
+                const int dg = r[7];
+                int st[kEllNb];
+#pragma unroll
+                for (int k = 0; k < kEllNb; ++k) st[k] = k < dg ? ldcg(vis_p(r[k])) : 0;
+#pragma unroll
+                for (int k = 0; k < kEllNb; ++k) found |= k < dg && st[k] == s;
+                if (!found && dg > kEllNb) {
+                    const int rp = __ldg(a->rowptr + w);
+                    for (int k = kEllNb; k < dg && !found; ++k) found = ldcg(vis_p(__ldg(a->adj + rp + k))) == s;
+                }
+            }
+            int tot;
+            const int ex = cta_scan(found ? 1 : 0, &tot);
+            if (tot) {
+                if (threadIdx.x == 0) sm->bc[0] = atomicAdd(tail, tot);
+                __syncthreads();
+                if (found) nxt[sm->bc[0] + ex] = w;
+                __syncthreads();
+            }
+            cnt += found ? 1 : 0;
+        }
+        accumulate(cnt, key);
+    }
+
+    // Stamps the F vertices of nxt with s (balanced slices), then a grid barrier.
+    __device__ bool stamp_level(int s, const int* nxt, int F) {
+        const int b = cta_rank(), B = cta_count();
+        const int lo = (int)((long long)F * b / B), hi = (int)((long long)F * (b + 1) / B);
+        for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) {
+            const int w = ldcg(nxt + i);
+            if (in_graph(w)) *vis_p(w) = s;
+            else fail(kErrInternal);
+        }
+        return barrier();
     }
 
     // ---------------- asynchronous levels-only sweep (whole grid) ----------------
@@ -763,7 +841,9 @@ struct Engine {
             int* tail = &c->qtail[ecc % 3];
             if (b == 0 && threadIdx.x == 0) c->qtail[(ecc + 1) % 3] = 0;
             const int lo = (int)((long long)F * b / B), hi = (int)((long long)F * (b + 1) / B);
-            expand_levels(s, cur, nullptr, lo, hi, nxt, nullptr, tail);
+            const bool bu = bottom_up(F, reached);
+            if (bu) expand_levels_bottom_up(s, cur, lo, hi, nxt, tail);
+            else expand_levels(s, cur, nullptr, lo, hi, nxt, nullptr, tail);
             tick(kPhExpand);
             ExResult r;
             if (!exchange(r)) return false;
@@ -773,6 +853,7 @@ struct Engine {
                 last_key = r.key;
                 return true;
             }
+            if (bu && !stamp_level(s, nxt, r.total)) return false;
             int* t = cur; cur = nxt; nxt = t;
             F = r.total;
             reached += r.total;
@@ -817,6 +898,67 @@ struct Engine {
 #pragma unroll
         for (int k = 0; k < kEllNb; ++k) mask |= (cl[k] == key ? 1u : 0u) << k;
         return mask;
+    }
+
+    // Labelled, bottom-up, step 1: every frontier vertex publishes its key in fkey, and the slice's
+    // min (degree, id) is accumulated, as in phase_a.
+    __device__ void publish_keys(int d, unsigned long long ord0, const Slice& s) {
+        const int T = blockDim.x;
+        unsigned long long mk = kKeyMax;
+        for (int j = (int)threadIdx.x; j < s.cnt; j += T) {
+            const int u = sid(s, j);
+            if (!in_graph(u)) {
+                fail(kErrInternal);
+                continue;
+            }
+            a->fkey[u] = level_key(d, ord0 + (unsigned long long)j);
+            mk = min(mk, pack_key(__ldg(a->deg + u), u));
+        }
+        accumulate(0, mk);
+    }
+
+    // The round-0 element of a slice and its row, which phase B expects from phase A.
+    __device__ void round0_row(const Slice& s, int& u0, int (&r0)[8]) const {
+        u0 = -1;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r0[k] = 0;
+        if ((int)threadIdx.x < s.cnt) {
+            const int u = sid(s, threadIdx.x);
+            if (in_graph(u)) {
+                u0 = u;
+                load_row(u, r0);
+            }
+        }
+    }
+
+    // Labelled, bottom-up, step 2 (after an exchange): every unclaimed vertex takes the smallest key
+    // published by a neighbour in level d (key tag d + 1) as its claim.
+    __device__ void claims_bottom_up(int d) {
+        const int T = blockDim.x, n = a->n;
+        const unsigned long long tag = (unsigned long long)(d + 1);
+        const int stride = cta_count() * T;
+        for (int i = cta_rank() * T + (int)threadIdx.x; i < n; i += stride) {
+            const int w = a->v0 + i;
+            if (ld_claim(w) != kClaimNone) continue;
+            int r[8];
+            load_row(w, r);
+            const int dg = r[7];
+            unsigned long long kk[kEllNb];
+#pragma unroll
+            for (int k = 0; k < kEllNb; ++k) kk[k] = k < dg ? __ldcg(a->fkey + r[k]) : 0ull;
+            unsigned long long best = kKeyMax;
+#pragma unroll
+            for (int k = 0; k < kEllNb; ++k)
+                if ((kk[k] >> a->obits) == tag && kk[k] < best) best = kk[k];
+            if (dg > kEllNb) {
+                const int rp = __ldg(a->rowptr + w);
+                for (int k = kEllNb; k < dg; ++k) {
+                    const unsigned long long x = __ldcg(a->fkey + __ldg(a->adj + rp + k));
+                    if ((x >> a->obits) == tag && x < best) best = x;
+                }
+            }
+            if (best != kKeyMax) *claim_p(w) = best;
+        }
     }
 
     // Phase A over a slice whose element j has key level_key(d, ord0 + j). Accumulates the min
@@ -1085,7 +1227,14 @@ struct Engine {
             const unsigned long long ord0 = (unsigned long long)b * slot;
             int u0;
             int r0[8];
-            phase_a(d, ord0, cur, u0, r0);
+            // bottom-up by the size of the previous level (this one's is known after the exchange)
+            const bool bu = bottom_up(prev_size, lstart - nv);
+            if (bu) {
+                publish_keys(d, ord0, cur);
+                round0_row(cur, u0, r0);
+            } else {
+                phase_a(d, ord0, cur, u0, r0);
+            }
             if (threadIdx.x == 0) atomicAdd(&sm->acc_cnt, cur.cnt);
             tick(kPhClaim);
             ExResult r;
@@ -1097,6 +1246,11 @@ struct Engine {
                 ecc = d - 1;
                 size = prev_start + prev_size - nv;
                 return true;
+            }
+            if (bu) {
+                claims_bottom_up(d);
+                if (!barrier()) return false;
+                tick(kPhClaim);
             }
             write_labels(cur, lstart + r.pre);
             tick(kPhLabels);
@@ -1175,7 +1329,11 @@ struct Engine {
         const int stride = cta_count() * blockDim.x;
         for (int i = cta_rank() * blockDim.x + threadIdx.x; i < size; i += stride) {
             const int v = ldcg(a->perm + (n - 1 - (nv + i)));
-            if (in_graph(v)) *claim_p(v) = kClaimNone;
+            if (!in_graph(v)) continue;
+            *claim_p(v) = kClaimNone;
+            if constexpr (kBottomUp) {
+                if (a->fkey) a->fkey[v] = 0;  // no stale level tag for the next sweep
+            }
         }
         return barrier();
     }

@@ -5,6 +5,6 @@
 
 namespace rcm {
 
-template __global__ void k_rcm_single<1024, false>(EngineArgs, int);
+template __global__ void k_rcm_single<1024, false, false>(EngineArgs, int);
 
 }  // namespace rcm

@@ -5,6 +5,6 @@
 
 namespace rcm {
 
-template __global__ void k_rcm_single<512, true>(EngineArgs, int);
+template __global__ void k_rcm_single<512, true, false>(EngineArgs, int);
 
 }  // namespace rcm

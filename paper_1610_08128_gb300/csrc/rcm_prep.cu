@@ -17,7 +17,7 @@ namespace rcm {
 __global__ void k_degree_validate(int n, int nnz, const int* __restrict__ rowptr, const int* __restrict__ colidx,
                                   int* __restrict__ deg, unsigned long long* __restrict__ claim, int* __restrict__ vis,
                                   int* __restrict__ bigrows, Ctl* ctl, int small_max,
-                                  unsigned long long* __restrict__ adist) {
+                                  unsigned long long* __restrict__ adist, unsigned long long* __restrict__ fkey) {
     __shared__ int s_max;
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
@@ -44,6 +44,7 @@ __global__ void k_degree_validate(int n, int nnz, const int* __restrict__ rowptr
         claim[v] = ~0ull;
         vis[v] = 0;
         if (adist) adist[v] = ~0ull;
+        if (fkey) fkey[v] = 0;
         local_max = max(local_max, d);
     }
     atomicMax(&s_max, local_max);

@@ -261,7 +261,7 @@ static rcm_status launch_request(Server* s, Request* r) {
         o.cluster = 1;
         o.grid_blocks = s->cluster_blocks;
         SingleLaunch sl;
-        const rcm_status ls = single_launch(r->n, o, &sl);
+        const rcm_status ls = single_launch(r->n, r->nnz, o, &sl);
         if (ls != RCM_OK) return ls;
         if (e == cudaSuccess) e = enqueue_single(r->n, r->nnz, rowptr, colidx, perm, ws, L, sl, nullptr, st);
         status_dev = (const int*)(ws + L.ctl + offsetof(Ctl, status));

@@ -21,7 +21,7 @@ constexpr int kComponentOnGrid = 1 << 18;
 
 // with_cc: also the arrays of the concurrent-components pass (the fixed no-allocation workspace
 // leaves them out and orders components one by one).
-SingleLayout single_layout(long long n, long long nnz, bool with_cc, bool with_async) {
+SingleLayout single_layout(long long n, long long nnz, bool with_cc, bool with_async, bool with_fkey) {
     SingleLayout L;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -37,7 +37,8 @@ SingleLayout single_layout(long long n, long long nnz, bool with_cc, bool with_a
     L.bigrows = take(sizeof(int) * (size_t)std::max(n, 1LL));
     L.adj = take(sizeof(int) * (size_t)std::max(nnz, 1LL));
     L.ell = take(sizeof(int4) * 2 * (size_t)std::max(n, 1LL));
-    L.adist = L.actl = 0;
+    L.adist = L.actl = L.fkey = 0;
+    if (with_fkey) L.fkey = take(sizeof(unsigned long long) * (size_t)std::max(n, 1LL));
     if (with_async) {
         L.adist = take(sizeof(unsigned long long) * (size_t)std::max(n, 1LL));
         L.actl = take(sizeof(AsyncCtl));
@@ -60,7 +61,8 @@ SingleLayout single_layout(long long n, long long nnz, bool with_cc, bool with_a
     return L;
 }
 
-// CTAs per SM of each kernel: widths 32..1024 level by level (0..5), 512 with asynchronous sweeps (6)
+// CTAs per SM of each kernel: widths 32..1024 top-down (0..5), 512 with asynchronous sweeps (6),
+// 512 with per-level bottom-up expansion (7)
 static int g_single_blocks_per_sm[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
 static std::mutex g_single_mu;
 
@@ -76,29 +78,31 @@ static int threads_index(int threads) {
     return -1;
 }
 
-// async: the instantiation with asynchronous levels-only sweeps (512 threads only)
-static const void* single_kernel(int threads, bool async = false) {
-    if (async) return (const void*)k_rcm_single<512, true>;
+// async: the instantiation with asynchronous levels-only sweeps; hybrid: the one with per-level
+// bottom-up expansion (both 512 threads only)
+static const void* single_kernel(int threads, bool async = false, bool hybrid = false) {
+    if (async) return (const void*)k_rcm_single<512, true, false>;
+    if (hybrid) return (const void*)k_rcm_single<512, false, true>;
     switch (threads) {
-        case 32: return (const void*)k_rcm_single<32, false>;
-        case 64: return (const void*)k_rcm_single<64, false>;
-        case 128: return (const void*)k_rcm_single<128, false>;
-        case 256: return (const void*)k_rcm_single<256, false>;
-        case 1024: return (const void*)k_rcm_single<1024, false>;
+        case 32: return (const void*)k_rcm_single<32, false, false>;
+        case 64: return (const void*)k_rcm_single<64, false, false>;
+        case 128: return (const void*)k_rcm_single<128, false, false>;
+        case 256: return (const void*)k_rcm_single<256, false, false>;
+        case 1024: return (const void*)k_rcm_single<1024, false, false>;
     }
-    return (const void*)k_rcm_single<512, false>;
+    return (const void*)k_rcm_single<512, false, false>;
 }
 
 constexpr int kSingleDynSmem = (int)((sizeof(unsigned long long) + sizeof(int)) * kCompSmem);
 
-static int single_blocks_per_sm(int threads, bool async = false) {
+static int single_blocks_per_sm(int threads, bool async = false, bool hybrid = false) {
     std::lock_guard<std::mutex> g(g_single_mu);
-    if (async && threads != 512) return 0;
-    const int idx = async ? 6 : threads_index(threads);
+    if ((async || hybrid) && threads != 512) return 0;
+    const int idx = async ? 6 : hybrid ? 7 : threads_index(threads);
     if (idx < 0) return 0;  // not a supported block size (the options check rejects it first)
     if (g_single_blocks_per_sm[idx] < 0) {
         int b = 0;
-        const void* k = single_kernel(threads, async);
+        const void* k = single_kernel(threads, async, hybrid);
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSingleDynSmem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, threads, kSingleDynSmem);
         g_single_blocks_per_sm[idx] = b;
@@ -111,13 +115,16 @@ static int single_blocks_per_sm(int threads, bool async = false) {
 static int g_cluster_max = -1;
 
 int single_cluster_max() {
-    if (single_blocks_per_sm(512) <= 0 || single_blocks_per_sm(512, true) <= 0) return 0;
+    if (single_blocks_per_sm(512) <= 0 || single_blocks_per_sm(512, true) <= 0 ||
+        single_blocks_per_sm(512, false, true) <= 0)
+        return 0;
     std::lock_guard<std::mutex> g(g_single_mu);
     if (g_cluster_max < 0) {
         g_cluster_max = 0;
         const void* k = single_kernel(512);
         cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         cudaFuncSetAttribute(single_kernel(512, true), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(single_kernel(512, false, true), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         for (int c : {16, 8}) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(c);
@@ -159,7 +166,7 @@ static const void* small_kernel(int threads) {
 // vertices on GB300; the best ranged from 128 on long 2D grids to 512 on many-component meshes.)
 static int small_default_threads(int) { return 256; }
 
-rcm_status single_launch(int n, const rcm_options& o, SingleLaunch* out) {
+rcm_status single_launch(int n, long long nnz, const rcm_options& o, SingleLaunch* out) {
     const DeviceInfo& di = device_info();
     SingleLaunch sl;
     // the shared-memory CTA engine: on request, or automatically for small graphs when no option
@@ -191,7 +198,13 @@ rcm_status single_launch(int n, const rcm_options& o, SingleLaunch* out) {
     if (threads_index(sl.threads) < 0) return RCM_ERR_INVALID_ARG;
     sl.async = o.async_sweeps > 0;
     if (sl.async && sl.threads != 512) return RCM_ERR_INVALID_ARG;
-    const int per_sm = single_blocks_per_sm(sl.threads, sl.async);
+    // per-level bottom-up expansion: on request, or automatically for patterns averaging at least
+    // 8 stored entries per row (low-diameter graphs, whose frontiers grow wide); otherwise the
+    // top-down kernel, which carries none of its code
+    if (o.expand_mode >= 2 && (sl.threads != 512 || sl.async)) return RCM_ERR_INVALID_ARG;
+    sl.hybrid = o.expand_mode >= 2 ||
+                (o.expand_mode == 0 && sl.threads == 512 && !sl.async && nnz >= 8LL * (long long)n);
+    const int per_sm = single_blocks_per_sm(sl.threads, sl.async, sl.hybrid);
     if (per_sm <= 0) return RCM_ERR_CUDA;
     sl.cluster = o.cluster != 0;
     if (sl.cluster) {
@@ -221,6 +234,7 @@ rcm_status single_launch(int n, const rcm_options& o, SingleLaunch* out) {
     sl.stall = o.debug_stall_barrier ? 1 : 0;
     sl.async_slots = o.debug_async_slots;
     sl.by_degree = o.row_order ? 0 : 1;
+    sl.expand_mode = o.expand_mode;
     *out = sl;
     return RCM_OK;
 }
@@ -239,6 +253,8 @@ cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* c
     // the asynchronous sweeps need their words in the layout; without them the sweeps run level by level
     const bool async = sl.async && !sl.small && L.adist != 0;
     unsigned long long* adist = async ? (unsigned long long*)(base + L.adist) : nullptr;
+    const bool hybrid = sl.hybrid && !sl.small && !async && L.fkey != 0;
+    unsigned long long* fkey = hybrid ? (unsigned long long*)(base + L.fkey) : nullptr;
 
     cudaError_t e = cudaSuccess;
     if (ev) e = cudaEventRecord(ev[0], s);
@@ -247,7 +263,7 @@ cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* c
         const int pb = 256;
         const int pgrid = (int)std::min<long long>((n + pb - 1) / pb, (long long)di.sms * 16);
         k_degree_validate<<<std::max(pgrid, 1), pb, 0, s>>>(n, (int)nnz, rowptr, colidx, deg, claim, vis, bigrows, ctl,
-                                                           kSmallRowMax, adist);
+                                                           kSmallRowMax, adist, fkey);
         k_sort_rows_small<<<std::max(pgrid, 1), pb, 0, s>>>(n, rowptr, colidx, deg, adj, ell, ctl, kSmallRowMax,
                                                            sl.by_degree);
         // rows longer than kSmallRowMax entries number at most nnz / (kSmallRowMax + 1)
@@ -296,6 +312,8 @@ cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* c
     args.cc_big = kComponentOnGrid;
     // work queue of the asynchronous sweeps: pool4 as 2n 64-bit slots (the level-by-level
     // frontier buffers and the union-find parents are not in use while such a sweep runs)
+    args.fkey = fkey;
+    args.expand_mode = sl.expand_mode;
     args.adist = adist;
     args.aq = async ? (unsigned long long*)pool4 : nullptr;
     args.actl = async ? (AsyncCtl*)(base + L.actl) : nullptr;
@@ -321,9 +339,9 @@ cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* c
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelExC(&cfg, single_kernel(sl.threads, async), kargs);
+        e = cudaLaunchKernelExC(&cfg, single_kernel(sl.threads, async, hybrid), kargs);
     } else {
-        e = cudaLaunchCooperativeKernel(single_kernel(sl.threads, async), dim3(sl.blocks), dim3(sl.threads), kargs,
+        e = cudaLaunchCooperativeKernel(single_kernel(sl.threads, async, hybrid), dim3(sl.blocks), dim3(sl.threads), kargs,
                                         kSingleDynSmem, s);
     }
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
@@ -336,9 +354,9 @@ rcm_status order_single(int32_t n, int64_t nnz, const int32_t* rowptr, const int
     rcm_options o{};
     if (opts) o = *opts;
     SingleLaunch sl;
-    rcm_status st = single_launch(n, o, &sl);
+    rcm_status st = single_launch(n, nnz, o, &sl);
     if (st != RCM_OK) return st;
-    const SingleLayout L = single_layout(n, nnz, true, sl.async && !sl.small);
+    const SingleLayout L = single_layout(n, nnz, true, sl.async && !sl.small, sl.hybrid && !sl.small);
     void* ws = nullptr;
     st = ws_alloc(&ws, L.total, s);
     if (st != RCM_OK) return st;
@@ -415,11 +433,11 @@ rcm_status order_single_noalloc(int32_t n, const int32_t* rowptr, const int32_t*
     if (nnz < 0) return RCM_ERR_BAD_CSR;
     if (nnz > kNoAllocMaxNnz) return RCM_ERR_TOO_LARGE;
     if (nnz > 0 && !colidx) return RCM_ERR_INVALID_ARG;
-    const SingleLayout L = single_layout(n, nnz, false);
+    const SingleLayout L = single_layout(n, nnz, false, false, false);
     if (L.total > kNoAllocBytes) return RCM_ERR_TOO_LARGE;
 
     SingleLaunch sl;
-    st = single_launch(n, rcm_options{}, &sl);
+    st = single_launch(n, nnz, rcm_options{}, &sl);
     if (st != RCM_OK) return st;
     char* base = (char*)ws;
     Ctl* ctl = (Ctl*)(base + L.ctl);

@@ -11,13 +11,16 @@ namespace rcm {
 // component arrays are absent).
 // adist / actl: the asynchronous levels-only sweeps' distance words and counters (0 = absent; the
 // sweeps' work queue reuses the frontier buffers of pool4).
+// fkey: the bottom-up expansion's frontier keys (0 = absent: top-down only).
 struct SingleLayout {
     size_t ctl, pool4, deg, claim, vis, bigrows, adj, ell, cc_size, cc_key, cc_roots, cc_gkey, cc_gidx, cc_tab,
-        adist, actl, total;
+        adist, actl, fkey, total;
     int cc_cap;
 };
 // with_async: include the asynchronous sweeps' arrays (only calls that ask for those sweeps).
-SingleLayout single_layout(long long n, long long nnz, bool with_cc = true, bool with_async = false);
+// with_fkey: include the bottom-up frontier keys (the fixed no-allocation workspace leaves them out).
+SingleLayout single_layout(long long n, long long nnz, bool with_cc = true, bool with_async = false,
+                           bool with_fkey = true);
 
 // Launch shape of the engine.
 //   small = true:    one CTA holding the graph's claims, stamps and rows in shared memory.
@@ -37,11 +40,13 @@ struct SingleLaunch {
     bool async = false;          // levels-only sweeps through the asynchronous work queue
     int async_slots = 0;         // its capacity (0 = 2n)
     int by_degree = 1;           // rows in (degree, id) order; 0 = stored order (sort-free variant)
+    int expand_mode = 0;         // rcm_options.expand_mode
+    bool hybrid = false;         // the kernel with per-level bottom-up expansion
 };
 
-// Derives the launch shape from options for a graph of n vertices; RCM_ERR_INVALID_ARG for
-// unsupported shapes.
-rcm_status single_launch(int n, const rcm_options& o, SingleLaunch* out);
+// Derives the launch shape from options for a graph of n vertices and nnz stored entries;
+// RCM_ERR_INVALID_ARG for unsupported shapes.
+rcm_status single_launch(int n, long long nnz, const rcm_options& o, SingleLaunch* out);
 
 // Largest cluster the engine can be launched as on this device (16 or 8), 0 if none.
 int single_cluster_max();

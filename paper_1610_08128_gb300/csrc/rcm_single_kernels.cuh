@@ -22,27 +22,29 @@ inline size_t small_vis_off(int n) { return align16(8 * (size_t)n); }
 inline size_t small_ell_off(int n) { return align16(small_vis_off(n) + 4 * (size_t)n); }
 inline size_t small_smem_bytes(int n) { return small_ell_off(n) + 32 * (size_t)n; }
 
-// kAsync: the engine with asynchronous levels-only sweeps (instantiated for 512 threads only).
-template <int kThreads, bool kAsync>
+// kAsync: the engine with asynchronous levels-only sweeps; kBottomUp: the engine that may run
+// whole-grid levels bottom-up. Both are instantiated for 512 threads only.
+template <int kThreads, bool kAsync, bool kBottomUp>
 __global__ void __launch_bounds__(kThreads, 1) k_rcm_single(EngineArgs args, int stall);
 template <int kThreads>
 __global__ void __launch_bounds__(kThreads, 1) k_rcm_small(EngineArgs args, int vis_off, int ell_off);
 
 #ifndef RCM_KERNEL_DEFINITIONS
-extern template __global__ void k_rcm_single<32, false>(EngineArgs, int);
-extern template __global__ void k_rcm_single<64, false>(EngineArgs, int);
-extern template __global__ void k_rcm_single<128, false>(EngineArgs, int);
-extern template __global__ void k_rcm_single<256, false>(EngineArgs, int);
-extern template __global__ void k_rcm_single<512, false>(EngineArgs, int);
-extern template __global__ void k_rcm_single<1024, false>(EngineArgs, int);
-extern template __global__ void k_rcm_single<512, true>(EngineArgs, int);
+extern template __global__ void k_rcm_single<32, false, false>(EngineArgs, int);
+extern template __global__ void k_rcm_single<64, false, false>(EngineArgs, int);
+extern template __global__ void k_rcm_single<128, false, false>(EngineArgs, int);
+extern template __global__ void k_rcm_single<256, false, false>(EngineArgs, int);
+extern template __global__ void k_rcm_single<512, false, false>(EngineArgs, int);
+extern template __global__ void k_rcm_single<1024, false, false>(EngineArgs, int);
+extern template __global__ void k_rcm_single<512, true, false>(EngineArgs, int);
+extern template __global__ void k_rcm_single<512, false, true>(EngineArgs, int);
 extern template __global__ void k_rcm_small<32>(EngineArgs, int, int);
 extern template __global__ void k_rcm_small<64>(EngineArgs, int, int);
 extern template __global__ void k_rcm_small<128>(EngineArgs, int, int);
 extern template __global__ void k_rcm_small<256>(EngineArgs, int, int);
 extern template __global__ void k_rcm_small<512>(EngineArgs, int, int);
 #else
-template <int kThreads, bool kAsync>
+template <int kThreads, bool kAsync, bool kBottomUp>
 __global__ void __launch_bounds__(kThreads, 1) k_rcm_single(EngineArgs args, int stall) {
     __shared__ EngineSmem smem;
     __shared__ int s_item;
@@ -51,7 +53,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rcm_single(EngineArgs args, int
     if (ld_volatile(&ctl->status) & kErrBadCsr) return;
     if (stall && blockIdx.x == 0) return;  // test hook: the other CTAs' first wait runs out
     const int n = args.n;
-    Engine<false, false, kAsync> e;
+    Engine<false, false, kAsync, kBottomUp> e;
     e.init(args, &smem);
     int Z = 0;
     if (!e.label_isolated(Z)) return;

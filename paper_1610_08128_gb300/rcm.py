@@ -43,6 +43,7 @@ class rcm_options(ctypes.Structure):
         ("async_sweeps", ctypes.c_int32),
         ("debug_async_slots", ctypes.c_int32),
         ("row_order", ctypes.c_int32),
+        ("expand_mode", ctypes.c_int32),
     ]
 
 

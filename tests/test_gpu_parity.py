@@ -160,6 +160,11 @@ OPTION_SETS = [
     {"async_sweeps": 1, "cluster": 1, "grid_blocks": 4},
     {"async_sweeps": -1, "executor": 1},
     {"executor": 1, "async_sweeps": 1, "debug_async_slots": 16},   # queue runs full: level-by-level fallback
+    {"expand_mode": 2, "narrow_threshold": -1},                    # bottom-up on every level
+    {"expand_mode": 2, "grid_blocks": 3, "narrow_threshold": -1, "fused_sweeps": -1},
+    {"expand_mode": 2, "executor": 1},                             # bottom-up on the whole-grid levels
+    {"expand_mode": 1, "narrow_threshold": -1},                    # top-down only
+    {"expand_mode": 3, "narrow_threshold": -1},                    # chosen per level
 ]
 
 
@@ -194,6 +199,29 @@ def test_async_sweeps_on_large_graphs():
     o.async_sweeps, o.block_threads = 1, 256
     pm = torch.empty(g.n, dtype=torch.int32, device="cuda")
     assert rcm.rcm_order_ex(g.n, rp, ci, pm, o, None) == rcm.RCM_ERR_INVALID_ARG
+
+
+def test_bottom_up_expansion_on_low_diameter_graphs():
+    """Large random graphs of small diameter, where frontiers hold a large part of the graph and
+    the automatic mode switches to bottom-up: top-down only, bottom-up everywhere and automatic
+    all give the oracle's order (also with two large components ordered on the grid)."""
+    rcm = rcm_mod()
+    big = [synth.random_graph(300000, 1200000, 91, connected=True), synth.random_graph(200000, 300000, 92)]
+    two = synth.concat([synth.random_graph(270000, 800000, 93, connected=True),
+                        synth.random_graph(280000, 900000, 94, connected=True)])
+    big.append(synth.permute(synth.Csr(two.n, two.rowptr, two.colidx), synth.random_permutation(two.n, 95)))
+    for g in big:
+        want = oracle.rcm(g.n, g.rowptr, g.colidx)
+        for mode in (0, 1, 2, 3):
+            assert np.array_equal(gpu_perm(g, {"expand_mode": mode}), want), mode
+        assert np.array_equal(gpu_perm(g, {"expand_mode": 2, "narrow_threshold": -1, "fused_sweeps": -1}), want)
+    rp, ci = to_dev(big[0])
+    o = rcm.rcm_options()
+    o.expand_mode = 4
+    pm = torch.empty(big[0].n, dtype=torch.int32, device="cuda")
+    assert rcm.rcm_order_ex(big[0].n, rp, ci, pm, o, None) == rcm.RCM_ERR_INVALID_ARG
+    o.expand_mode, o.block_threads = 3, 256
+    assert rcm.rcm_order_ex(big[0].n, rp, ci, pm, o, None) == rcm.RCM_ERR_INVALID_ARG
 
 
 def test_sort_free_variant_matches_the_oracle_variant():
