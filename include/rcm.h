@@ -117,6 +117,9 @@ typedef struct {
                                   Modes 2 and 3 need 512-thread CTAs and level-by-level sweeps
                                   (else RCM_ERR_INVALID_ARG; 0 then means 1). Narrow levels and the
                                   CTA executors are always top-down.                                */
+    int32_t bottom_up_divisor; /* switch threshold of expand_mode 3 (and 0 when it picks 3): a level
+                                  runs bottom-up when its frontier holds at least n / divisor vertices
+                                  and at least a quarter of those not yet reached; 0 = 16          */
 } rcm_options;
 
 /* Statistics of one ordering (filled by rcm_order_ex when requested). */

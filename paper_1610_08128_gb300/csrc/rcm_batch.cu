@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(kThreads) k_rcm_batch(BatchArgs b) {
         a.limit_ns = 0;
         a.fkey = nullptr;  // CTA engines: top-down, level by level
         a.expand_mode = 1;
+        a.bu_divisor = 16;
         a.adist = nullptr;
         a.aq = nullptr;
         a.actl = nullptr;

@@ -86,6 +86,7 @@ struct EngineArgs {
     // bottom-up expansion (whole-grid executor only; fkey == null: top-down only)
     unsigned long long* fkey;    // n words: a labelled frontier vertex's key, published for bottom-up claims
     int expand_mode;             // 2 = bottom-up on every grid level, 1 = top-down, else per level by frontier size
+    int bu_divisor;              // per level: bottom-up once the frontier holds n / bu_divisor vertices
     // asynchronous levels-only sweeps (whole-grid executor only; adist == null: level by level)
     unsigned long long* adist;   // n words: (~sweep stamp) << 32 | breadth-first distance
     unsigned long long* aq;      // work queue of aq_cap (distance << 32 | vertex) items
@@ -435,7 +436,7 @@ struct Engine {
         if constexpr (!kBottomUp) return false;
         if (!a->fkey || a->expand_mode == 1) return false;
         if (a->expand_mode == 2) return true;
-        return F * 16 >= a->n && F * 4 >= (long long)a->n - seen;
+        return F * a->bu_divisor >= a->n && F * 4 >= (long long)a->n - seen;
     }
 
     // Levels-only, bottom-up: every vertex not stamped s with a stamped neighbour is appended to

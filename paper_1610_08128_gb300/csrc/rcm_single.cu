@@ -235,6 +235,7 @@ rcm_status single_launch(int n, long long nnz, const rcm_options& o, SingleLaunc
     sl.async_slots = o.debug_async_slots;
     sl.by_degree = o.row_order ? 0 : 1;
     sl.expand_mode = o.expand_mode;
+    sl.bu_divisor = o.bottom_up_divisor > 0 ? o.bottom_up_divisor : 16;
     *out = sl;
     return RCM_OK;
 }
@@ -314,6 +315,7 @@ cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* c
     // frontier buffers and the union-find parents are not in use while such a sweep runs)
     args.fkey = fkey;
     args.expand_mode = sl.expand_mode;
+    args.bu_divisor = sl.bu_divisor;
     args.adist = adist;
     args.aq = async ? (unsigned long long*)pool4 : nullptr;
     args.actl = async ? (AsyncCtl*)(base + L.actl) : nullptr;

@@ -42,6 +42,7 @@ struct SingleLaunch {
     int by_degree = 1;           // rows in (degree, id) order; 0 = stored order (sort-free variant)
     int expand_mode = 0;         // rcm_options.expand_mode
     bool hybrid = false;         // the kernel with per-level bottom-up expansion
+    int bu_divisor = 16;         // bottom-up once the frontier holds n / bu_divisor vertices
 };
 
 // Derives the launch shape from options for a graph of n vertices and nnz stored entries;

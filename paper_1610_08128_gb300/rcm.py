@@ -44,6 +44,7 @@ class rcm_options(ctypes.Structure):
         ("debug_async_slots", ctypes.c_int32),
         ("row_order", ctypes.c_int32),
         ("expand_mode", ctypes.c_int32),
+        ("bottom_up_divisor", ctypes.c_int32),
     ]
 
 

@@ -2,8 +2,8 @@
 
 Every tunable is a plain option of the C ABI and changes speed only: the batched executor's CTA
 width and row-sort split (rcm_batch_options), and the one-graph executor, CTA width,
-frontier-switch threshold, sweep mode (level by level or asynchronous) and expansion mode
-(top-down or chosen per level) (rcm_options). The tuner times each candidate on the caller's own data
+frontier-switch threshold, sweep mode (level by level or asynchronous), expansion mode (top-down
+or chosen per level) and the top-down/bottom-up switch threshold (rcm_options). The tuner times each candidate on the caller's own data
 through the C ABI (CUDA events, median of a few runs after one warm-up), checks that every
 candidate returns the same permutation as the first one, and returns the fastest. Choices can be
 cached per device and size class in a JSON file.
@@ -24,8 +24,10 @@ SINGLE_CANDIDATES = [
     {"executor": 1, "async_sweeps": a, **({"narrow_threshold": t} if t else {})}
     for a in (1, -1) for t in (0, 128, 256, 512, 2048)
 ] + [
-    {"executor": 1, "expand_mode": e, **({"narrow_threshold": t} if t else {})}
-    for e in (1, 3) for t in (0, 512)
+    {"executor": 1, "expand_mode": 1, **({"narrow_threshold": t} if t else {})} for t in (0, 512)
+] + [
+    {"executor": 1, "expand_mode": 3, "bottom_up_divisor": dv, **({"narrow_threshold": t} if t else {})}
+    for dv in (4, 16, 64) for t in (0, 512)
 ] + [
     {"executor": 2, "block_threads": 128},
     {"executor": 2, "block_threads": 256},

@@ -165,6 +165,7 @@ OPTION_SETS = [
     {"expand_mode": 2, "executor": 1},                             # bottom-up on the whole-grid levels
     {"expand_mode": 1, "narrow_threshold": -1},                    # top-down only
     {"expand_mode": 3, "narrow_threshold": -1},                    # chosen per level
+    {"expand_mode": 3, "bottom_up_divisor": 1000000},              # per level, switching early
 ]
 
 
