@@ -11,6 +11,16 @@ def test_candidates_are_valid_option_sets():
         if c["executor"] == 2:
             assert 32 <= c["block_threads"] <= 512
     assert len({tuple(sorted(c.items())) for c in tune.SINGLE_CANDIDATES}) == len(tune.SINGLE_CANDIDATES)
+    from paper_1610_08128_gb300 import rcm
+
+    fields = {f for f, _ in rcm.rcm_options._fields_}
+    bfields = {f for f, _ in rcm.rcm_batch_options._fields_}
+    for c in tune.SINGLE_CANDIDATES:
+        assert set(c) <= fields, c
+        # per-level expansion and asynchronous sweeps are separate 512-thread engines
+        assert not (c.get("expand_mode", 0) >= 2 and c.get("async_sweeps", 0) == 1), c
+    for c in tune.BATCH_CANDIDATES:
+        assert set(c) <= bfields, c
 
 
 def test_size_class_buckets_powers_of_four():
