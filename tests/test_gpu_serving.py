@@ -76,10 +76,12 @@ def test_served_results_equal_single_calls(rcm):
 def test_large_requests_run_on_a_cluster(rcm):
     """Requests of 2^18 vertices or more run the persistent engine launched as one thread-block
     cluster, mixed with small requests on single CTAs; every result equals the oracle and
-    rcm_order alone."""
+    rcm_order alone. The random graph (about 10 entries per row) runs the engine with per-level
+    bottom-up expansion on its cluster."""
     big = [synth.grid((70, 70, 70), seed=11), synth.grid((600, 600), seed=12),
-           synth.batch_graph(2, 300000, [503, 0])]
-    small = mix(9, 503)
+           synth.batch_graph(2, 300000, [503, 0]), synth.random_graph(280000, 1100000, 504, connected=True)]
+    small = mix(12, 503)
+    assert len(small[0::3]) == len(big)
     graphs = [g for pair in zip(big, small[0::3]) for g in pair] + small[1::3] + small[2::3]
     st, srv = rcm.rcm_server_create(8 << 30, 32)
     rcm.check(st, "create")
