@@ -57,12 +57,59 @@ __device__ __forceinline__ unsigned long long row_key(const int* __restrict__ de
     return pack_key(by_degree ? __ldg(deg + w) : p, w);
 }
 
+__device__ __forceinline__ void cmp_swap(unsigned long long& x, unsigned long long& y) {
+    const unsigned long long lo = x < y ? x : y;
+    y = x < y ? y : x;
+    x = lo;
+}
+
+// Rows of at most 8 stored entries (every row of the grids and meshes): keys in registers, sorted
+// by Batcher's 8-input odd-even merge network (19 compare-exchanges, no indexed local array).
+// Absent and diagonal entries get the largest key and sort to the end. Keys are unique, so the
+// order equals the insertion sort's.
+__device__ __forceinline__ void sort_row8(int v, int a, int len, const int* __restrict__ colidx,
+                                          const int* __restrict__ deg, int* __restrict__ adj,
+                                          int4* __restrict__ ell, int by_degree) {
+    unsigned long long k[8];
+    int m = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        k[i] = kKeyMax;
+        if (i < len) {
+            const int w = colidx[a + i];
+            if (w != v) {
+                k[i] = row_key(deg, w, i, by_degree);
+                ++m;
+            }
+        }
+    }
+    cmp_swap(k[0], k[1]); cmp_swap(k[2], k[3]); cmp_swap(k[4], k[5]); cmp_swap(k[6], k[7]);
+    cmp_swap(k[0], k[2]); cmp_swap(k[1], k[3]); cmp_swap(k[4], k[6]); cmp_swap(k[5], k[7]);
+    cmp_swap(k[1], k[2]); cmp_swap(k[5], k[6]);
+    cmp_swap(k[0], k[4]); cmp_swap(k[1], k[5]); cmp_swap(k[2], k[6]); cmp_swap(k[3], k[7]);
+    cmp_swap(k[2], k[4]); cmp_swap(k[3], k[5]);
+    cmp_swap(k[1], k[2]); cmp_swap(k[3], k[4]); cmp_swap(k[5], k[6]);
+    int r[8];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) r[i] = i < m ? (int)(unsigned)(k[i] & 0xffffffffu) : -1;
+    r[7] = m;
+    store_ell(ell, v, r);
+    if (m > 7) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) adj[a + i] = (int)(unsigned)(k[i] & 0xffffffffu);
+    }
+}
+
 // Sorted row of a vertex with at most kSmallRowMax stored entries, by one thread: the padded row
 // and, for degree > 7, the full sorted row in adj (same offsets as the input row).
 __device__ __forceinline__ void sort_small_row(int v, const int* __restrict__ rowptr, const int* __restrict__ colidx,
                                                const int* __restrict__ deg, int* __restrict__ adj,
                                                int4* __restrict__ ell, int by_degree) {
     const int a = rowptr[v], b = rowptr[v + 1];
+    if (b - a <= 8) {
+        sort_row8(v, a, b - a, colidx, deg, adj, ell, by_degree);
+        return;
+    }
     unsigned long long key[kSmallRowMax];
     int m = 0;
     for (int k = a; k < b; ++k) {
