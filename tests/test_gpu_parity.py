@@ -413,12 +413,18 @@ def test_batch_rejects_cross_block_entries():
 
 @pytest.mark.slow
 def test_c2_grid192_full_size():
-    """The full 192^3 workload, in the launch configurations the benchmark's tuner chooses from
-    (frontier-switch thresholds of the persistent grid)."""
+    """The full 192^3 workload in every launch configuration the benchmark's autotuner chooses from
+    (frontier switches, sweep and expansion modes), and the sort-free variant against the oracle's."""
+    from paper_1610_08128_gb300 import tune
+
     g = synth.c2_grid3d()
     want = oracle.rcm(g.n, g.rowptr, g.colidx)
-    for opts in [None, {"narrow_threshold": 128}, {"narrow_threshold": 256}, {"narrow_threshold": 512}]:
+    assert np.array_equal(gpu_perm(g), want)
+    for opts in tune.SINGLE_CANDIDATES:
+        if opts["executor"] == 2:
+            continue  # the shared-memory CTA takes at most 4,608 vertices
         assert np.array_equal(gpu_perm(g, opts), want), opts
+    assert np.array_equal(gpu_perm(g, {"row_order": 1}), oracle.rcm(g.n, g.rowptr, g.colidx, row_order=1))
 
 
 @pytest.mark.slow
