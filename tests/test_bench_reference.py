@@ -1,5 +1,5 @@
-"""The benchmark's reference arm (the serial oracle on the host) prints the contract's JSON line;
-checked on a small grid so that it runs in a second on CPU."""
+"""The benchmark's reference arm (the serial oracle on the host) prints the contract's JSON line,
+checked on a small grid so that it runs in a second on CPU; and the bench's host-side helpers."""
 import json
 import os
 import subprocess
@@ -23,3 +23,25 @@ def test_reference_arm_prints_one_contract_line():
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["n"] == 16 ** 3
+
+
+def test_bench_launch_options_and_traffic_record():
+    """--launch parses key=value pairs or JSON into engine options; the recorded DRAM traffic is
+    reported only for the kernel sources it was captured from."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1610_08128_gb300 import rcm
+
+    assert bench.parse_launch("executor=1,narrow_threshold=512") == {"executor": 1, "narrow_threshold": 512}
+    assert bench.parse_launch('{"expand_mode": 3}') == {"expand_mode": 3}
+    assert bench.parse_launch("") == {}
+    a, b = rcm.rcm_options(), rcm.rcm_options()
+    a.narrow_threshold, a.expand_mode, a.nnz = 512, 3, 99
+    bench.ctypes_copy(a, b)
+    assert (b.narrow_threshold, b.expand_mode, b.nnz) == (512, 3, 99)
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        rec = json.load(f)["k_rcm_single"]["grid192"]
+    assert rec["dram_bytes_per_launch"] == rec["dram_bytes_read"] + rec["dram_bytes_write"]
+    if rec["sources"] == bench.kernel_sources_hash():
+        assert bench.recorded_traffic("k_rcm_single", "grid192") == rec["dram_bytes_per_launch"]
+    assert bench.recorded_traffic("k_rcm_single", "grid7") is None
