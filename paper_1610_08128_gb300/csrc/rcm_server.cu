@@ -42,7 +42,7 @@ namespace rcm {
 // (see the header comment). Small clusters measured best on GB300: they leave room on the SMs for
 // the single-CTA requests, while each large request keeps most of the speed of a wide grid.
 constexpr long long kServeClusterMin = 1LL << 18;
-constexpr int kServeClusterBlocks = 4;
+constexpr int kServeClusterBlocks = 6;
 
 // Arena bytes of one request: the staged CSR and result when they are in host memory, a 256-byte
 // header holding the graph offsets {0, n} of a batch of one, and the larger of the two executors'
