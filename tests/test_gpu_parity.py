@@ -368,13 +368,27 @@ def test_bandwidth_profile_matches_oracle():
 
 
 def test_order_host_end_to_end():
+    """Host buffers, pinned and pageable, including sizes that are not a multiple of 16 bytes and a
+    pinned buffer at an odd 4-byte offset."""
     rcm = rcm_mod()
-    for g in [synth.c1_grid2d(), synth.c3_mesh(10000), synth.csr_from_edges(5, [], [])]:
-        rp = torch.from_numpy(g.rowptr.copy()).pin_memory()
-        ci = torch.from_numpy(g.colidx.copy() if g.nnz else np.zeros(1, np.int32)).pin_memory()
+    for g in [synth.c1_grid2d(), synth.c3_mesh(10000), synth.csr_from_edges(5, [], []), synth.grid((7, 9), seed=4),
+              synth.c3_mesh(300001)]:
+        want = oracle.rcm(g.n, g.rowptr, g.colidx)
+        ci_np = g.colidx.copy() if g.nnz else np.zeros(1, np.int32)
+        for pinned in (True, False):
+            rp = torch.from_numpy(g.rowptr.copy())
+            ci = torch.from_numpy(ci_np.copy())
+            pm = torch.empty(g.n, dtype=torch.int32)
+            if pinned:
+                rp, ci, pm = rp.pin_memory(), ci.pin_memory(), pm.pin_memory()
+            rcm.check(rcm.rcm_order_host(g.n, rp, ci, pm), "rcm_order_host")
+            assert np.array_equal(pm.numpy(), want), pinned
+        # a pinned buffer whose data starts 4 bytes into its allocation
+        big = torch.zeros(len(ci_np) + 1, dtype=torch.int32).pin_memory()
+        big[1:] = torch.from_numpy(ci_np)
         pm = torch.empty(g.n, dtype=torch.int32).pin_memory()
-        rcm.check(rcm.rcm_order_host(g.n, rp, ci, pm), "rcm_order_host")
-        assert np.array_equal(pm.numpy(), oracle.rcm(g.n, g.rowptr, g.colidx))
+        rcm.check(rcm.rcm_order_host(g.n, torch.from_numpy(g.rowptr.copy()).pin_memory(), big[1:], pm), "offset")
+        assert np.array_equal(pm.numpy(), want)
 
 
 def test_batch_matches_oracle_and_single():
