@@ -289,12 +289,20 @@ def served_setup(args, torch, rcm, synth, workers):
         t0 = time.perf_counter()
         rcm.check(rcm.rcm_order_host(g.n, r, c, out), "plain")
         service.append(time.perf_counter() - t0)
-    fin, lat = 0.0, []
-    for t_a, gi in zip(arrival, which):
-        fin = max(fin, t_a) + service[gi]
-        lat.append(fin - t_a)
-    return {"arrival": arrival, "which": which, "pool": pool, "bufs": bufs, "fifo_rate": len(arrival) / fin,
+    rate, lat = fifo_schedule(arrival, [service[gi] for gi in which])
+    return {"arrival": arrival, "which": which, "pool": pool, "bufs": bufs, "fifo_rate": rate,
             "fifo_p50": pct(lat, 0.5), "fifo_p99": pct(lat, 0.99)}
+
+
+def fifo_schedule(arrival, service):
+    """One server taking requests in arrival order: request k starts when it has arrived and the
+    previous one has finished, and runs for service[k]. Returns (requests per second over the
+    whole schedule, each request's latency from arrival to finish)."""
+    fin, lat = 0.0, []
+    for t_a, t_s in zip(arrival, service):
+        fin = max(fin, t_a) + t_s
+        lat.append(fin - t_a)
+    return (len(lat) / fin if fin > 0 else 0.0), lat
 
 
 def served_run(args, torch, rcm, setup, options=None, check=True, max_inflight=256):

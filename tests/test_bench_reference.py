@@ -45,3 +45,16 @@ def test_bench_launch_options_and_traffic_record():
     if rec["sources"] == bench.kernel_sources_hash():
         assert bench.recorded_traffic("k_rcm_single", "grid192") == rec["dram_bytes_per_launch"]
     assert bench.recorded_traffic("k_rcm_single", "grid7") is None
+
+
+def test_fifo_schedule_of_the_served_baseline():
+    """The FIFO baseline of the served line: one request at a time in arrival order."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    rate, lat = bench.fifo_schedule([0.0, 0.1, 0.15, 5.0], [1.0, 0.5, 0.25, 1.0])
+    # finishes at 1.0, 1.5, 1.75 (queued behind each other), then 6.0 (the server was idle)
+    assert [round(x, 9) for x in lat] == [1.0, 1.4, 1.6, 1.0]
+    assert abs(rate - 4 / 6.0) < 1e-12
+    assert bench.fifo_schedule([], []) == (0.0, [])
+    assert bench.pct([3.0, 1.0, 2.0], 0.5) == 2.0 and bench.pct([], 0.5) is None
