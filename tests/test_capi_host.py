@@ -108,3 +108,23 @@ def test_binding_structures_match_the_header(tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(st), name
         for f, _ in st._fields_:
             assert got[(name, f)] == getattr(st, f).offset, (name, f)
+
+
+def test_option_checks_come_before_any_device_work(lib):
+    """Invalid options and sizes are refused with RCM_ERR_INVALID_ARG before the call touches a
+    device (so this runs on a host without one); n = 0 with valid options is a no-op."""
+    from paper_1610_08128_gb300 import rcm
+
+    bad = [("expand_mode", 4), ("expand_mode", -1), ("row_order", 2), ("async_sweeps", 2), ("async_sweeps", -2),
+           ("bottom_up_divisor", -1), ("debug_async_slots", -1), ("executor", 3), ("cluster", 2),
+           ("block_threads", 100), ("narrow_threshold", -2), ("grid_blocks", -1), ("spin_limit_ns", -1)]
+    for field, value in bad:
+        o = rcm.rcm_options()
+        setattr(o, field, value)
+        assert rcm.rcm_order_ex(0, None, None, None, o, None) == rcm.RCM_ERR_INVALID_ARG, field
+    assert rcm.rcm_order_ex(-1, None, None, None, None, None) == rcm.RCM_ERR_INVALID_ARG
+    assert rcm.rcm_order_ex(0, None, None, None, rcm.rcm_options(), None) == rcm.RCM_OK
+    rep = rcm.rcm_validate_report()
+    assert rcm.rcm_validate(-1, None, None, rep) == rcm.RCM_ERR_INVALID_ARG
+    assert rcm.rcm_validate(0, None, None, rep) == rcm.RCM_OK
+    assert rep.first_bad_row == -1 and rep.duplicates == 0 and rep.asymmetric == 0
