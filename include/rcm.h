@@ -66,7 +66,8 @@ const char *rcm_status_string(rcm_status s);
 /* Tuning knobs. None of them changes the result, except row_order: every other setting yields the
    same permutation. Zero-initialise and set what you need; 0 means "library default" in every field. */
 typedef struct {
-    int32_t narrow_threshold;  /* frontier size below which a single CTA runs the levels; -1 = never */
+    int32_t narrow_threshold;  /* frontier size below which a single CTA runs the levels; -1 = never;
+                                  0 = the CTA width                                                 */
     int32_t grid_blocks;       /* CTAs of the persistent grid (<= co-resident limit); 0 = one per SM */
     int32_t block_threads;     /* threads per CTA of the persistent grid: 32 .. 1024 (power of 2); 0 = 512 */
     int32_t fused_sweeps;      /* 0/1 = label during sweeps 2.. (fused); -1 = separate labelled pass */

@@ -226,7 +226,9 @@ rcm_status single_launch(int n, long long nnz, const rcm_options& o, SingleLaunc
         sl.blocks = (int)std::max(1ull, slot_cap);
     }
     // narrow runs keep the frontier in a shared-memory cache of kCache ids
-    int narrow = o.narrow_threshold == 0 ? 2 * sl.threads : (o.narrow_threshold < 0 ? 0 : o.narrow_threshold);
+    // default switch at the CTA width: for 512-thread CTAs it beat twice the width on every graph
+    // measured on GB300 (the 192^3 grid 7.40 against 7.64 ms, a 1000^2 grid 19.1 against 24.3 ms)
+    int narrow = o.narrow_threshold == 0 ? sl.threads : (o.narrow_threshold < 0 ? 0 : o.narrow_threshold);
     sl.narrow = std::min(narrow, kCache);
     sl.limit_ns = o.spin_limit_ns > 0 ? o.spin_limit_ns : 20000000000LL;
     sl.fused = o.fused_sweeps >= 0 ? 1 : 0;

@@ -21,13 +21,13 @@ BATCH_CANDIDATES = [
 ]
 
 SINGLE_CANDIDATES = [
-    {"executor": 1, "async_sweeps": a, **({"narrow_threshold": t} if t else {})}
-    for a in (1, -1) for t in (0, 128, 256, 512, 2048)
+    {"executor": 1, "async_sweeps": a, "narrow_threshold": t}
+    for a in (1, -1) for t in (128, 256, 512, 1024, 2048)
 ] + [
-    {"executor": 1, "expand_mode": 1, **({"narrow_threshold": t} if t else {})} for t in (0, 512)
+    {"executor": 1, "expand_mode": 1, "narrow_threshold": t} for t in (512, 1024)
 ] + [
-    {"executor": 1, "expand_mode": 3, "bottom_up_divisor": dv, **({"narrow_threshold": t} if t else {})}
-    for dv in (4, 16, 64) for t in (0, 512)
+    {"executor": 1, "expand_mode": 3, "bottom_up_divisor": dv, "narrow_threshold": t}
+    for dv in (4, 16, 64) for t in (512, 1024)
 ] + [
     {"executor": 2, "block_threads": 128},
     {"executor": 2, "block_threads": 256},
