@@ -233,8 +233,11 @@ rcm_status rcm_batch_plan_destroy(rcm_batch_plan *plan);
  * every GPU that loads the library until the process exits).
  *   Limits   n <= 65,536 vertices and rowptr[n] <= 1,048,576 stored entries; larger patterns
  *            return RCM_ERR_TOO_LARGE before any work is enqueued.
- *   Set-up   the first call on a device looks up the array's device address (once per device,
- *            with that device current); make that first call before any stream capture.
+ *   Set-up   the first call on a device does a one-time set-up with that device current: it looks
+ *            up the array's device address and loads every kernel the call can launch (CUDA
+ *            loads device code lazily, and loading takes device memory). So that first call may
+ *            allocate; later calls allocate nothing. Make the first call on each device at
+ *            start-up, before the memory budget is handed out, and before any stream capture.
  *   Sharing  every call uses the same array, which keeps the previous call's contents (the call
  *            clears what must start at zero). Calls whose work overlaps on the GPU (different
  *            streams, or host threads) race on it and must be serialised by the caller.

@@ -401,8 +401,31 @@ static __device__ __align__(256) unsigned char g_noalloc_ws[kNoAllocBytes];
 // Device address of g_noalloc_ws on the current device. In host code the symbol itself is only a
 // host-side stand-in, so the address is looked up once per device (with that device current)
 // and cached.
+//
+// That first call per device is also the set-up of everything else the path needs once: CUDA
+// loads device code lazily (a module when one of its kernels or variables is first used), and
+// loading it takes device memory. So the set-up loads every kernel the path can launch, and the
+// host-side launch attributes of both executors, before the address is cached; later calls load
+// nothing. (The first launch of the row sorter may also grow the context's local memory for its
+// stack frame; every call launches it, so the first call does that too.)
 static std::mutex g_noalloc_mu;
 static void* g_noalloc_ptr[64];
+
+static rcm_status noalloc_setup() {
+    const void* kernels[] = {(const void*)k_degree_validate, (const void*)k_sort_rows_small,
+                             (const void*)k_sort_rows_big, small_kernel(small_default_threads(0)),
+                             single_kernel(512)};
+    for (const void* k : kernels) {
+        cudaFuncAttributes fa;
+        const cudaError_t e = cudaFuncGetAttributes(&fa, k);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    // one-time attribute set-up of the shared-memory CTA and of the persistent grid
+    SingleLaunch sl;
+    rcm_status st = single_launch(1, 0, rcm_options{}, &sl);
+    if (st == RCM_OK) st = single_launch(kSmallMaxN + 1, 0, rcm_options{}, &sl);
+    return st;
+}
 
 static rcm_status noalloc_workspace(void** out) {
     int dev = 0;
@@ -414,6 +437,8 @@ static rcm_status noalloc_workspace(void** out) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_ws);
         if (e != cudaSuccess || !p) return e != cudaSuccess ? cuda_status(e) : RCM_ERR_CUDA;
+        const rcm_status st = noalloc_setup();
+        if (st != RCM_OK) return st;
         g_noalloc_ptr[dev] = p;
     }
     *out = g_noalloc_ptr[dev];

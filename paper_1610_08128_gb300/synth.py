@@ -11,7 +11,8 @@ through ``SeedSequence``.
 
 Conventions (Sec. III, graph of A): vertex v is row/column v; an undirected edge {i, j} appears as
 both (i, j) and (j, i); there are no duplicate entries; diagonal entries appear only when asked for
-(they carry no edge). Column indices inside a row are sorted ascending.
+(they carry no edge). Column indices inside a row are sorted ascending, except after
+:func:`shuffle_rows` and in :func:`csr_from_rows`, which keep a given stored order.
 """
 from __future__ import annotations
 
@@ -99,6 +100,52 @@ def random_permutation(n: int, seed) -> np.ndarray:
     return rng_for(seed).permutation(n).astype(np.int64)
 
 
+def shuffle_rows(g: Csr, seed) -> Csr:
+    """The same pattern with the entries of every row stored in a seeded random order.
+
+    A CSR pattern is a set of nonzeros per row (Sec. III-A); the order inside a row is free. The
+    other generators store rows sorted by column id, which this undoes."""
+    rng = rng_for(seed)
+    lens = np.diff(g.rowptr.astype(np.int64))
+    rows = np.repeat(np.arange(g.n, dtype=np.int64), lens)
+    order = np.lexsort((rng.random(g.nnz), rows))
+    meta = dict(g.meta)
+    meta["row_shuffle"] = seed
+    return Csr(g.n, g.rowptr.copy(), g.colidx[order].astype(np.int32), meta)
+
+
+def csr_from_rows(rows) -> Csr:
+    """CSR from explicit stored rows (a list of column lists), keeping each row's order as given."""
+    lens = np.array([len(r) for r in rows], dtype=np.int64)
+    rowptr = np.zeros(len(rows) + 1, dtype=np.int64)
+    rowptr[1:] = np.cumsum(lens)
+    colidx = np.array([c for r in rows for c in r], dtype=np.int32)
+    return Csr(len(rows), rowptr.astype(np.int32), colidx)
+
+
+def power_law(n: int, avg_degree: float, gamma: float, seed) -> Csr:
+    """Chung-Lu random graph with a power-law expected degree sequence.
+
+    Vertex i (before the id permutation) gets weight w_i proportional to (i + i0)^(-1/(gamma-1)),
+    scaled so the weights average ``avg_degree``; n * avg_degree / 2 edges are drawn with both
+    endpoints chosen with probability proportional to weight (duplicates and self pairs dropped).
+    A few hub rows hold thousands of entries, as in the scale-free matrices of circuit and network
+    problems. Ids are permuted uniformly from the seed."""
+    rng = rng_for(seed)
+    i0 = 10.0  # keeps the largest weight finite and the top hubs a few thousand strong at n = 10^6
+    w = (np.arange(n, dtype=np.float64) + i0) ** (-1.0 / (gamma - 1.0))
+    w *= avg_degree * n / w.sum()
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    m = int(round(n * avg_degree / 2))
+    src = np.minimum(np.searchsorted(cdf, rng.random(m), side="right"), n - 1)
+    dst = np.minimum(np.searchsorted(cdf, rng.random(m), side="right"), n - 1)
+    g = csr_from_edges(n, src, dst)
+    g = permute(g, rng.permutation(n))
+    g.meta = {"kind": "power_law", "n": n, "avg_degree": avg_degree, "gamma": gamma, "seed": seed}
+    return g
+
+
 def _grid_natural(dims) -> Csr:
     """5-point (2D) / 7-point (3D) stencil pattern on a regular grid, natural C-order ids."""
     dims = tuple(int(d) for d in dims)
@@ -171,6 +218,19 @@ def grid_fast(dims, seed=None) -> Csr:
 def path(n: int, seed=None) -> Csr:
     g = csr_from_edges(n, np.arange(n - 1), np.arange(1, n)) if n > 1 else csr_from_edges(n, [], [])
     g.meta = {"kind": "path", "seed": seed}
+    if seed is not None:
+        g = permute(g, random_permutation(n, seed))
+    return g
+
+
+def circulant(n: int, offsets, seed=None) -> Csr:
+    """Circulant pattern: vertex v joined to v + k and v - k (mod n) for every k in ``offsets``, so
+    each row holds exactly 2 * len(offsets) entries when n > 2 * max(offsets). With a seed, ids are
+    permuted uniformly."""
+    src = np.repeat(np.arange(n, dtype=np.int64), len(offsets))
+    dst = (src + np.tile(np.asarray(offsets, dtype=np.int64), n)) % n
+    g = csr_from_edges(n, src, dst)
+    g.meta = {"kind": "circulant", "offsets": list(map(int, offsets)), "seed": seed}
     if seed is not None:
         g = permute(g, random_permutation(n, seed))
     return g

@@ -140,6 +140,97 @@ def test_components_concurrent_with_a_grid_sized_one():
     assert_parity(synth.permute(synth.Csr(g2.n, g2.rowptr, g2.colidx), synth.random_permutation(g2.n, 64)))
 
 
+def golden(name):
+    """A pattern from tests/golden (explicit stored rows, or an edge list) and its expected perm."""
+    import os
+
+    d = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                k, v = line.split(":", 1)
+                d.setdefault(k.strip(), []).extend(int(x) for x in v.split())
+    n = d["n"][0]
+    if "rowptr" in d:
+        g = synth.Csr(n, np.array(d["rowptr"], np.int32), np.array(d["colidx"], np.int32))
+    else:
+        e = np.array(d["edges"], np.int64).reshape(-1, 2)
+        g = synth.csr_from_edges(n, e[:, 0], e[:, 1])
+    return g, np.array(d["perm"], np.int32)
+
+
+def star(leaves, centre=0):
+    others = np.array([v for v in range(leaves + 1) if v != centre], np.int64)
+    return synth.csr_from_edges(leaves + 1, np.full(leaves, centre, np.int64), others)
+
+
+def shuffled_graphs():
+    """Patterns whose rows are stored in a seeded random order (the order inside a row is free):
+    grids, meshes with and without components, random graphs, stars whose centre row is longer
+    than the per-thread sorters (8 and 32 entries) and than the shared-memory sorter, a power-law
+    graph with hubs of thousands of entries, and random small graphs."""
+    base = [synth.c1_grid2d(), synth.grid((20, 30, 11), seed=3), synth.c3_mesh(20000),
+            synth.c3_mesh(8000, stitch=False), synth.knn_mesh(30000, 3, 11), synth.random_graph(3000, 4000, 9),
+            star(40, 17), star(5000, 2500), star(20000), synth.power_law(60000, 10, 2.5, 112),
+            golden("broom78.txt")[0]]
+    base += small_graphs(60, 400, 111)
+    return [synth.shuffle_rows(g, [4242, i]) for i, g in enumerate(base)]
+
+
+def test_rows_stored_in_any_order():
+    """Exact mode on rows stored in shuffled order: the row sort (register network for rows of at
+    most 8 entries, insertion sort up to 32, a whole CTA beyond) must recover the (degree, id) order
+    of Alg. 1 from any stored order, on the persistent grid and the shared-memory CTA."""
+    for g in shuffled_graphs():
+        want = oracle.rcm(g.n, g.rowptr, g.colidx)
+        assert_parity(g)
+        assert np.array_equal(gpu_perm(g, {"executor": 1}), want)
+        assert np.array_equal(gpu_perm(g, {"executor": 1, "narrow_threshold": -1}), want)
+        if g.n <= 4608:
+            assert np.array_equal(gpu_perm(g, {"executor": 2}), want)
+
+
+def test_rows_stored_in_any_order_every_expansion():
+    """The same on low-diameter shuffled graphs with every expansion mode and asynchronous sweeps."""
+    graphs = [synth.shuffle_rows(g, [4243, i]) for i, g in
+              enumerate([synth.random_graph(200000, 900000, 113, connected=True), synth.power_law(200000, 12, 2.3, 114)])]
+    for g in graphs:
+        want = oracle.rcm(g.n, g.rowptr, g.colidx)
+        for opts in ({"expand_mode": 1}, {"expand_mode": 2}, {"expand_mode": 3}, {"async_sweeps": 1},
+                     {"expand_mode": 2, "narrow_threshold": -1, "fused_sweeps": -1}):
+            assert np.array_equal(gpu_perm(g, opts), want), opts
+
+
+@pytest.mark.parametrize("name", ["star41_shuffled.txt", "star41_reversed.txt", "broom78.txt"])
+def test_wide_row_fixtures(name):
+    """The hand-worked wide-row fixtures (rows of more than 32 neighbours, stored out of order)."""
+    g, perm = golden(name)
+    for opts in (None, {"executor": 1}, {"executor": 2}, {"executor": 1, "narrow_threshold": -1}):
+        assert np.array_equal(gpu_perm(g, opts), perm), opts
+
+
+def test_batch_rows_stored_in_any_order():
+    """The batched engine on shuffled rows, with every row-sort split and CTA width."""
+    rcm = rcm_mod()
+    graphs = [g for g in shuffled_graphs() if g.n <= 30000]
+    b = synth.concat(graphs)
+    goff = torch.from_numpy(b.goff).cuda()
+    rp = torch.from_numpy(b.rowptr).cuda()
+    ci = torch.from_numpy(b.colidx).cuda()
+    want = [oracle.rcm(g.n, g.rowptr, g.colidx) for g in graphs]
+    for threads in (128, 256, 512):
+        for split in (4, 8, 32):
+            o = rcm.rcm_batch_options()
+            o.block_threads, o.row_sort_split = threads, split
+            perm = torch.full((b.n,), -1, dtype=torch.int32, device="cuda")
+            rcm.check(rcm.rcm_order_batch_ex(len(graphs), b.n, goff, rp, ci, perm, o), "batch_ex")
+            rcm.check(rcm.rcm_stream_status(), "batch_ex")
+            host = perm.cpu().numpy()
+            for gi in range(len(graphs)):
+                assert np.array_equal(host[b.goff[gi]:b.goff[gi + 1]], want[gi]), (threads, split, gi)
+
+
 OPTION_SETS = [
     {"narrow_threshold": -1},            # whole grid for every level
     {"narrow_threshold": 1 << 30},       # CTA 0 for every level

@@ -106,6 +106,35 @@ def test_large_requests_run_on_a_cluster(rcm):
         rcm.check(rcm.rcm_server_destroy(srv), "destroy")
 
 
+def test_served_rows_stored_in_any_order(rcm):
+    """Requests whose rows are stored in shuffled order (the order inside a row is free): small
+    requests on single CTAs, stars with rows longer than the per-thread sorters, and a request large
+    enough for the cluster engine; each result equals the oracle."""
+    star = synth.csr_from_edges(6001, np.zeros(6000, np.int64), np.arange(1, 6001))
+    base = mix(16, 505) + [star, synth.csr_from_edges(41, np.full(40, 17, np.int64),
+                                                       np.array([v for v in range(41) if v != 17])),
+                           synth.grid((70, 70, 70), seed=13)]
+    graphs = [synth.shuffle_rows(g, [506, i]) for i, g in enumerate(base)]
+    st, srv = rcm.rcm_server_create(8 << 30, 32)
+    rcm.check(st, "create")
+    try:
+        keep, tickets = [], []
+        for g in graphs:
+            o = torch.empty(g.n, dtype=torch.int32).pin_memory()
+            rp, ci = torch.from_numpy(g.rowptr).pin_memory(), torch.from_numpy(g.colidx).pin_memory()
+            s, t = rcm.rcm_submit(srv, g.n, g.nnz, rp, ci, o)
+            rcm.check(s, "submit")
+            keep.append((rp, ci, o))
+            tickets.append(t)
+        for g, t, (_, _, o) in zip(graphs, tickets, keep):
+            rcm.check(rcm.rcm_wait(srv, t), "wait")
+            assert np.array_equal(o.numpy(), oracle.rcm(g.n, g.rowptr, g.colidx))
+        _, info = rcm.rcm_server_info(srv)
+        assert info["failed"] == 0
+    finally:
+        rcm.check(rcm.rcm_server_destroy(srv), "destroy")
+
+
 def test_admission_under_a_small_budget(rcm):
     graphs = mix(12, 502, lo=20000, hi=40000)
     need = max(region_bytes(g) for g in graphs)

@@ -533,16 +533,61 @@ def read_golden(name):
     return data
 
 
-@pytest.mark.parametrize("name", ["star6.txt", "grid3x3.txt", "path6.txt", "two_components.txt"])
+def golden_graph(d):
+    """The fixture's pattern: an undirected edge list (rows sorted by id), or explicit stored rows
+    (rowptr / colidx, kept in the order the fixture gives them)."""
+    n = int(d["n"][0])
+    if "rowptr" in d:
+        return synth.Csr(n, np.array(d["rowptr"], dtype=np.int32), np.array(d["colidx"], dtype=np.int32))
+    e = np.array(d.get("edges", []), dtype=np.int64).reshape(-1, 2)
+    return synth.csr_from_edges(n, e[:, 0], e[:, 1])
+
+
+HAND_WORKED = ["star6.txt", "grid3x3.txt", "path6.txt", "two_components.txt"]
+# rows with more than 32 neighbours to number, stored out of id order
+WIDE_ROWS = ["star41_shuffled.txt", "star41_reversed.txt", "broom78.txt"]
+
+
+@pytest.mark.parametrize("name", HAND_WORKED + WIDE_ROWS)
 def test_hand_worked_fixtures(name):
     d = read_golden(name)
-    n = int(d["n"][0])
-    e = np.array(d.get("edges", []), dtype=np.int64).reshape(-1, 2)
-    g = synth.csr_from_edges(n, e[:, 0], e[:, 1])
+    g = golden_graph(d)
     p = rcm_of(g)
     assert list(p) == [int(x) for x in d["perm"]]
     if "bandwidth" in d:
         assert oracle.bandwidth_profile(g.n, g.rowptr, g.colidx, p) == (int(d["bandwidth"][0]), int(d["profile"][0]))
+
+
+@pytest.mark.parametrize("name", WIDE_ROWS)
+def test_wide_row_fixtures_are_symmetric_stored_out_of_order(name):
+    """The wide-row fixtures are valid patterns (symmetric, no duplicates or diagonal), have a row
+    with more than 32 entries, and store at least one row out of ascending id order, so that they
+    reach the oracle's branch for long neighbour lists with unsorted input."""
+    g = golden_graph(read_golden(name))
+    pairs = set()
+    unsorted = False
+    for v in range(g.n):
+        row = [int(w) for w in g.colidx[g.rowptr[v]:g.rowptr[v + 1]]]
+        assert len(set(row)) == len(row) and v not in row
+        unsorted |= row != sorted(row)
+        pairs |= {(v, w) for w in row}
+    assert all((w, v) in pairs for v, w in pairs)
+    assert np.diff(g.rowptr).max() > 33 and unsorted
+
+
+@pytest.mark.parametrize("name", WIDE_ROWS)
+def test_wide_row_fixtures_match_level_form(name):
+    """The same fixtures through the independent level-synchronous restatement of Alg. 3/Alg. 4
+    (numpy lexsort, not the oracle's sort)."""
+    g = golden_graph(read_golden(name))
+    deg = oracle.degrees(g.n, g.rowptr, g.colidx).astype(np.int64)
+    r0 = int(np.lexsort((np.arange(g.n), deg))[0])
+    root, _, _ = alg4_level_synchronous(g, deg, r0)
+    R = np.full(g.n, -1, dtype=np.int64)
+    assert alg3_level_synchronous(g, deg, root, 0, R) == g.n
+    seq = np.empty(g.n, dtype=np.int64)
+    seq[R] = np.arange(g.n)
+    assert list(seq[::-1]) == [int(x) for x in read_golden(name)["perm"]]
 
 
 def test_regression_fixture_written_from_oracle():
@@ -576,6 +621,16 @@ MUTANTS = {
     "one_sweep_only": ("    while (ecc_r > nlvl) {", "    while (0) {"),
     "bandwidth_f_starts_at_zero": ("int32_t v = perm[i], f = i;", "int32_t v = perm[i], f = 0;"),
     "sort_free_still_sorts": ("        if (!by_degree) {", "        if (0) {"),
+    # the branch that sorts more than 32 neighbours at once (packed (degree, id) keys)
+    "wide_rows_tie_break_highest_id": (
+        "                keys[i] = ((uint64_t)(uint32_t)deg[scratch[i]] << 32) | (uint32_t)scratch[i];\n"
+        "            qsort(keys, (size_t)found, sizeof(uint64_t), cmp_key);\n"
+        "            for (int32_t i = 0; i < found; ++i) scratch[i] = (int32_t)(keys[i] & 0xffffffffu);",
+        "                keys[i] = ((uint64_t)(uint32_t)deg[scratch[i]] << 32) | (uint32_t)(0x7fffffff - scratch[i]);\n"
+        "            qsort(keys, (size_t)found, sizeof(uint64_t), cmp_key);\n"
+        "            for (int32_t i = 0; i < found; ++i) scratch[i] = 0x7fffffff - (int32_t)(keys[i] & 0xffffffffu);"),
+    "wide_rows_by_id_only": ("keys[i] = ((uint64_t)(uint32_t)deg[scratch[i]] << 32) | (uint32_t)scratch[i];",
+                             "keys[i] = (uint64_t)(uint32_t)scratch[i];"),
     "start_at_highest_degree": ("while (label[start_order[cursor]] >= 0) cursor++;\n        int32_t r0 = start_order[cursor];",
                                 "int32_t r0 = -1;\n        for (int32_t c = n - 1; c >= 0; --c) if (label[start_order[c]] < 0) { r0 = start_order[c]; break; }"),
 }
@@ -602,6 +657,11 @@ def _pins_with(lib):
             sols = enumerate_cm_sequences(adj, deg, george_liu_roots(adj, deg))
             p = oracle.rcm(g.n, g.rowptr, g.colidx, lib=lib)
             if len(sols) != 1 or list(p[::-1]) != sols[0]:
+                return False
+        for name in HAND_WORKED + WIDE_ROWS:
+            d = read_golden(name)
+            g = golden_graph(d)
+            if list(oracle.rcm(g.n, g.rowptr, g.colidx, lib=lib)) != [int(x) for x in d["perm"]]:
                 return False
         rp = np.array([0, 5, 6, 7, 8, 9, 10], np.int32)          # the stored-order star above
         ci = np.array([5, 4, 3, 2, 1, 0, 0, 0, 0, 0], np.int32)

@@ -61,3 +61,25 @@ def test_trace_shape():
     arr, which, pool = synth.c5_trace(requests=50, pool=4, nmin=100, nmax=2000)
     assert len(arr) == 50 and np.all(np.diff(arr) >= 0) and arr[0] == 0
     assert which.max() < 4 and len(pool) == 4
+
+
+def test_shuffle_rows_keeps_each_row_set_and_is_seeded():
+    g = synth.grid((9, 11), seed=3)
+    a, b, c = synth.shuffle_rows(g, 1), synth.shuffle_rows(g, 1), synth.shuffle_rows(g, 2)
+    assert np.array_equal(a.rowptr, g.rowptr) and np.array_equal(a.colidx, b.colidx)
+    assert not np.array_equal(a.colidx, c.colidx)
+    for v in range(g.n):
+        lo, hi = g.rowptr[v], g.rowptr[v + 1]
+        assert sorted(a.colidx[lo:hi]) == list(g.colidx[lo:hi])
+
+
+def test_power_law_and_circulant_patterns():
+    g = synth.power_law(20000, 10, 2.5, 3)
+    lens = np.diff(g.rowptr)
+    assert lens.max() > 200 and np.median(lens) < 20          # hubs and a light tail
+    rows = np.repeat(np.arange(g.n), lens)
+    keys = set(zip(rows.tolist(), g.colidx.tolist()))
+    assert all((c, r) in keys for r, c in keys) and all(r != c for r, c in keys)
+    assert len(keys) == g.nnz                                 # no duplicates
+    c = synth.circulant(1000, range(1, 4), seed=2)
+    assert c.nnz == 6000 and set(np.diff(c.rowptr).tolist()) == {6}
