@@ -70,7 +70,8 @@ typedef struct {
                                   0 = the CTA width                                                 */
     int32_t grid_blocks;       /* CTAs of the persistent grid (<= co-resident limit); 0 = one per SM */
     int32_t block_threads;     /* threads per CTA of the persistent grid: 32 .. 1024 (power of 2); 0 = 512 */
-    int32_t fused_sweeps;      /* 0/1 = label during sweeps 2.. (fused); -1 = separate labelled pass */
+    int32_t fused_sweeps;      /* 0/1 = label during sweeps 2.. (fused); 2 = label during every sweep,
+                                  the first included; -1 = separate labelled pass                  */
     int64_t spin_limit_ns;     /* bound of every device-side wait; 0 = 20 s                        */
     int64_t nnz;               /* rowptr[n] when the caller knows it: skips the synchronised 4-byte
                                   read (the device still checks it; a mismatch is RCM_ERR_BAD_CSR);
@@ -121,6 +122,10 @@ typedef struct {
     int32_t bottom_up_divisor; /* switch threshold of expand_mode 3 (and 0 when it picks 3): a level
                                   runs bottom-up when its frontier holds at least n / divisor vertices
                                   and at least a quarter of those not yet reached; 0 = 16          */
+    int32_t l2_persist;        /* 1 = the persistent grid's launch marks its claim and stamp arrays
+                                  (12 bytes per vertex) as persisting in L2, through an access-policy
+                                  window; this sets the context's persisting-L2 limit to the window's
+                                  size (at most the device maximum). 0 or -1 = off                  */
 } rcm_options;
 
 /* Statistics of one ordering (filled by rcm_order_ex when requested). */

@@ -1369,7 +1369,19 @@ struct Engine {
         int ecc_prev;
         unsigned long long k1;
         long long reached;
-        if (!sweep_levels(r, ecc_prev, k1, reached)) return false;
+        if (a->fused == 2) {
+            // the first sweep labelled as well: a labelled traversal gives the same eccentricity and
+            // last level as a levels-only one, and its level code is the faster of the two on the
+            // whole grid. Its labels are discarded.
+            int sz = 0;
+            if (!sweep_labelled(r, nv, ecc_prev, k1, sz)) return false;
+            reached = sz;
+            tick(kPhOther);
+            if (!reset_claims(nv, sz)) return false;
+            tick(kPhOther);
+        } else if (!sweep_levels(r, ecc_prev, k1, reached)) {
+            return false;
+        }
         if (all_left >= 0 && reached < all_left) {
             size = -1;
             return true;

@@ -231,15 +231,52 @@ rcm_status single_launch(int n, long long nnz, const rcm_options& o, SingleLaunc
     int narrow = o.narrow_threshold == 0 ? sl.threads : (o.narrow_threshold < 0 ? 0 : o.narrow_threshold);
     sl.narrow = std::min(narrow, kCache);
     sl.limit_ns = o.spin_limit_ns > 0 ? o.spin_limit_ns : 20000000000LL;
-    sl.fused = o.fused_sweeps >= 0 ? 1 : 0;
+    sl.fused = o.fused_sweeps < 0 ? 0 : (o.fused_sweeps == 2 ? 2 : 1);
     sl.profile = o.profile_phases ? 1 : 0;
     sl.stall = o.debug_stall_barrier ? 1 : 0;
+    sl.l2_persist = o.l2_persist > 0;
     sl.async_slots = o.debug_async_slots;
     sl.by_degree = o.row_order ? 0 : 1;
     sl.expand_mode = o.expand_mode;
     sl.bu_divisor = o.bottom_up_divisor > 0 ? o.bottom_up_divisor : 16;
     *out = sl;
     return RCM_OK;
+}
+
+// The cooperative launch of the persistent grid with [win, win + bytes) -- the claim and stamp
+// arrays, which every level's atomics hit at random -- marked persisting in L2, so that the rows
+// streaming through L2 do not evict them. The context's persisting-L2 limit is raised to the
+// window (clamped to the device maximum) on first use.
+static cudaError_t launch_persisting(const void* kernel, const SingleLaunch& sl, void** kargs, char* win, size_t bytes,
+                                     cudaStream_t s) {
+    int dev = 0, max_persist = 0, max_window = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev);
+    if (e != cudaSuccess) return e;
+    const size_t window = std::min(bytes, (size_t)max_window);
+    const size_t persist = std::min(window, (size_t)max_persist);
+    size_t cur = 0;
+    e = cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+    if (e == cudaSuccess && cur < persist) e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, persist);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(sl.blocks);
+    cfg.blockDim = dim3(sl.threads);
+    cfg.dynamicSmemBytes = kSingleDynSmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    attr[1].id = cudaLaunchAttributeAccessPolicyWindow;
+    attr[1].val.accessPolicyWindow.base_ptr = win;
+    attr[1].val.accessPolicyWindow.num_bytes = window;
+    attr[1].val.accessPolicyWindow.hitRatio = window ? std::min(1.0f, (float)persist / (float)window) : 0.0f;
+    attr[1].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    attr[1].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelExC(&cfg, kernel, kargs);
 }
 
 cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* colidx, int* perm, char* base,
@@ -344,6 +381,9 @@ cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* c
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         e = cudaLaunchKernelExC(&cfg, single_kernel(sl.threads, async, hybrid), kargs);
+    } else if (sl.l2_persist) {
+        e = launch_persisting(single_kernel(sl.threads, async, hybrid), sl, kargs, base + L.claim,
+                              L.bigrows - L.claim, s);
     } else {
         e = cudaLaunchCooperativeKernel(single_kernel(sl.threads, async, hybrid), dim3(sl.blocks), dim3(sl.threads), kargs,
                                         kSingleDynSmem, s);

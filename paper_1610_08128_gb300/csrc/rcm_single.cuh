@@ -34,7 +34,7 @@ struct SingleLaunch {
     bool small = false;          // one CTA with the graph's state in shared memory (k_rcm_small)
     int narrow = 0;              // frontier size below which CTA 0 runs levels alone
     long long limit_ns = 20000000000LL;
-    int fused = 1;
+    int fused = 1;               // 0 = separate labelled pass, 1 = labelled sweeps 2.., 2 = every sweep labelled
     int profile = 0;
     int stall = 0;
     bool async = false;          // levels-only sweeps through the asynchronous work queue
@@ -43,6 +43,7 @@ struct SingleLaunch {
     int expand_mode = 0;         // rcm_options.expand_mode
     bool hybrid = false;         // the kernel with per-level bottom-up expansion
     int bu_divisor = 16;         // bottom-up once the frontier holds n / bu_divisor vertices
+    bool l2_persist = false;     // claims and stamps marked persisting in L2 for the engine's launch
 };
 
 // Derives the launch shape from options for a graph of n vertices and nnz stored entries;

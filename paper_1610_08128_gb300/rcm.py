@@ -45,6 +45,7 @@ class rcm_options(ctypes.Structure):
         ("row_order", ctypes.c_int32),
         ("expand_mode", ctypes.c_int32),
         ("bottom_up_divisor", ctypes.c_int32),
+        ("l2_persist", ctypes.c_int32),
     ]
 
 
