@@ -56,19 +56,33 @@ def parse_args():
     p.add_argument("--serve-requests", type=int, default=4000)
     p.add_argument("--serve-pool", type=int, default=256)
     p.add_argument("--serve-rate", type=float, default=2000.0)
+    p.add_argument("--fifo-requests", type=int, default=500,
+                   help="requests of the served trace replayed FIFO through rcm_order_host (a prefix)")
+    p.add_argument("--no-configs", action="store_true", help="skip the 64x64 grid, mesh and power-law lines")
     p.add_argument("--launch", default=None,
                    help="options of the one-graph engine, skipping the autotuner: key=value pairs such as "
                         "executor=1,narrow_threshold=512 (or a JSON object)")
     return p.parse_args()
 
 
-def algorithmic_bytes(n: int, nnz: int, levels_only: int, labelled: int) -> int:
+def algorithmic_bytes(n: int, nnz: int, levels_only: float, labelled: float, reverse: bool = True) -> int:
     """Bytes per ordering of the traversal kernel: per levels-only sweep 4(n+1) rowptr + 4nnz
     colidx + 4nnz neighbour-state gather + 4n level write + 8n queue write/read; a labelled sweep
-    adds 4n degree + 4n parent + 16n key write/read + 4n label."""
+    adds 4n degree + 4n parent + 16n key write/read + 4n label; the fused reversal writes 8n."""
     b_sweep = 4 * (n + 1) + 4 * nnz + 4 * nnz + 4 * n + 8 * n
     b_lab = b_sweep + 4 * n + 4 * n + 16 * n + 4 * n
-    return levels_only * b_sweep + labelled * b_lab
+    return int(levels_only * b_sweep + labelled * b_lab + (8 * n if reverse else 0))
+
+
+def method_traversals(stats: dict) -> tuple[float, float, float]:
+    """(levels-only sweeps, labelled traversals, traversals) that the method needs, in units of
+    whole-graph traversals: every component's sweeps but its last are levels-only (Alg. 2), the
+    last is the labelled one (Alg. 3), whatever the engine chose to label. Components are taken
+    as equally swept: sweeps / components traversals of each, so that a component's share of the
+    graph counts once per sweep (exact for one component)."""
+    comps = max(1, stats["components"] - stats["isolated"])
+    per = stats["sweeps"] / comps
+    return per - 1.0, 1.0, per
 
 
 def load_peaks():
@@ -188,6 +202,64 @@ def gpu_uuid(torch):
         return None
 
 
+def timed_orderings(rcm, torch, n, rp, ci, perm, opts, steps, flush, stream):
+    """Median device time (ms) of `steps` orderings (CUDA events on the launching stream, L2 flushed
+    between them), the traversal kernel's median time and the last call's statistics."""
+    step_ms, trav_ms, st = [], [], None
+    for i in range(steps):
+        flush.fill_(i)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st = rcm.rcm_stats()
+        e0.record(stream)
+        rcm.check(rcm.rcm_order_ex(n, rp, ci, perm, opts, st, stream), "rcm_order_ex")
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        trav_ms.append(st.traverse_ms)
+    return statistics.median(step_ms), statistics.median(trav_ms), st.as_dict()
+
+
+def bench_config(name, g, args, rcm, torch, flush, peak, oracle_orderings=1):
+    """One more single-graph workload: tuned launch, device time per ordering, GTEPS, the traversal
+    kernel's roofline and the serial oracle on one host core (its CPU baseline)."""
+    from paper_1610_08128_gb300 import tune
+
+    stream = torch.cuda.current_stream()
+    rp = torch.from_numpy(g.rowptr).cuda()
+    ci = torch.from_numpy(g.colidx if g.nnz else np.zeros(1, np.int32)).cuda()
+    perm = torch.empty(max(g.n, 1), dtype=torch.int32, device="cuda")
+    tuned, _ = tune.tune_single(g.n, rp, ci, perm, nnz=g.nnz, repeats=2)
+    opts = rcm.rcm_options()
+    opts.nnz = g.nnz
+    for k, v in tuned.items():
+        setattr(opts, k, v)
+    for _ in range(2):
+        rcm.check(rcm.rcm_order_ex(g.n, rp, ci, perm, opts, None, stream), "warm-up")
+    step, trav, st = timed_orderings(rcm, torch, g.n, rp, ci, perm, opts, max(5, args.steps), flush, stream)
+    offdiag = g.offdiag_nnz()
+    m = offdiag // 2
+    lo, lab, per = method_traversals(st)
+    alg = algorithmic_bytes(g.n, offdiag, lo, lab)
+    out = {"workload": name, "n": g.n, "nnz": g.nnz, "launch": tuned, "ms_per_ordering": step, "kernel_ms": trav,
+           "GTEPS": per * m / (step / 1e3) / 1e9,
+           "roofline": {"bound": "hbm", "achieved": alg / (trav / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": alg / (trav / 1e3) / 1e9 / peak, "algorithmic_bytes": alg, "kernel": "k_rcm_single"},
+           "stats": {k: st[k] for k in ("components", "sweeps", "levels", "max_ecc", "isolated", "narrow_levels",
+                                       "grid_levels")}}
+    if not args.no_cpu_baseline:
+        import oracle
+
+        ts = []
+        for _ in range(oracle_orderings):
+            t0 = time.perf_counter()
+            oracle.rcm(g.n, g.rowptr, g.colidx)
+            ts.append(time.perf_counter() - t0)
+        out["cpu_baseline"] = {"value": per * m / statistics.mean(ts) / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"{oracle_orderings} serial ordering(s) of the full workload",
+                               "ms_per_ordering": statistics.mean(ts) * 1e3}
+    return out
+
+
 def make_workload(side: int):
     from paper_1610_08128_gb300 import synth
 
@@ -266,7 +338,32 @@ def bench_batched(args, torch, rcm, synth, workers, rank=0, world=1, dist=None):
     host = perm.cpu().numpy()
     same = all(np.array_equal(host[b.goff[gi]:b.goff[gi + 1]], pm.cpu().numpy()[:b.graphs[gi].n])
                for gi, (_, _, _, pm) in zip(sample, dev))
+    out_extra = {}
+    if not args.no_cpu_baseline and rank == 0:
+        # the oracle over all host cores, one graph per thread, on the whole batch; its per-graph
+        # sweep counts also give the batch's algorithmic bytes (every graph's sweeps but the last
+        # are levels-only, the last labelled, plus the reversal)
+        import oracle
+
+        cores = len(os.sched_getaffinity(0))
+        t0 = time.perf_counter()
+        res = oracle.rcm_batch(b.goff, b.rowptr, b.colidx, threads=cores, with_stats=True)
+        t_cpu = time.perf_counter() - t0
+        alg = 0
+        for gi, g in enumerate(b.graphs):
+            stg = res[gi][1]
+            lo, lab, _ = method_traversals(dict(stg, isolated=stg["isolated"]))
+            alg += algorithmic_bytes(g.n, g.offdiag_nnz(), lo, lab) if g.n else 0
+        peak, peak_kind = load_peaks()
+        out_extra["cpu_baseline"] = {"value": b.G / t_cpu, "unit": "orderings/s", "cores": cores, "kind": "oracle",
+                                     "sample": f"all {b.G} graphs of the batch, one graph per thread"}
+        out_extra["roofline"] = {"bound": "hbm", "achieved": alg / t / 1e9, "peak": peak, "unit": "GB/s",
+                                 "frac": alg / t / 1e9 / peak, "algorithmic_bytes": alg,
+                                 "bytes_per_vertex": alg / b.n, "kernel": "k_rcm_batch",
+                                 "time": "whole replay (the batch kernel's share is in the committed launch list)",
+                                 "peak_kind": f"{peak_kind} hbm_gbs (copy)"}
     return {"workload": f"{b.G} graphs per GPU, n log-uniform 100..50,000, 2D grid / 3D grid / kNN(3) mesh",
+            **out_extra,
             "vertices": b.n, "entries": int(b.rowptr[-1]), "ms": t * 1e3, "orderings_per_s": world * b.G / t,
             "plain_orderings_per_s": 1.0 / t_plain, "plain_sample": len(dev), "vs_plain": (b.G / t) * t_plain,
             "sample_equal_to_plain": bool(same), "tuned": best,
@@ -278,31 +375,38 @@ def bench_batched(args, torch, rcm, synth, workers, rank=0, world=1, dist=None):
 
 def served_setup(args, torch, rcm, synth, workers):
     """The served trace (Poisson arrivals over a pool of graphs, pinned host buffers) and the same
-    trace served FIFO by rcm_order_host, simulated from per-graph service times measured here."""
+    trace's first requests served FIFO through rcm_order_host, replayed in real time."""
     arrival, which, pool = synth.c5_trace(requests=args.serve_requests, rate_per_s=args.serve_rate,
                                           pool=args.serve_pool, workers=workers)
     bufs = [(torch.from_numpy(g.rowptr).pin_memory(), torch.from_numpy(g.colidx).pin_memory()) for g in pool]
-    service = []
-    for g, (r, c) in zip(pool, bufs):
-        out = torch.empty(g.n, dtype=torch.int32).pin_memory()
-        rcm.check(rcm.rcm_order_host(g.n, r, c, out), "plain")
-        t0 = time.perf_counter()
-        rcm.check(rcm.rcm_order_host(g.n, r, c, out), "plain")
-        service.append(time.perf_counter() - t0)
-    rate, lat = fifo_schedule(arrival, [service[gi] for gi in which])
+    prefix = min(len(arrival), args.fifo_requests)
+    outs = {int(gi): torch.empty(pool[int(gi)].n, dtype=torch.int32).pin_memory() for gi in set(which[:prefix].tolist())}
+
+    def plain(gi):
+        g = pool[gi]
+        rcm.check(rcm.rcm_order_host(g.n, bufs[gi][0], bufs[gi][1], outs[gi]), "plain")
+
+    for gi in list(outs)[:4]:  # warm-up of the call path
+        plain(gi)
+    rate, lat = fifo_replay(arrival[:prefix], which[:prefix], plain)
     return {"arrival": arrival, "which": which, "pool": pool, "bufs": bufs, "fifo_rate": rate,
-            "fifo_p50": pct(lat, 0.5), "fifo_p99": pct(lat, 0.99)}
+            "fifo_p50": pct(lat, 0.5), "fifo_p99": pct(lat, 0.99), "fifo_requests": prefix}
 
 
-def fifo_schedule(arrival, service):
-    """One server taking requests in arrival order: request k starts when it has arrived and the
-    previous one has finished, and runs for service[k]. Returns (requests per second over the
-    whole schedule, each request's latency from arrival to finish)."""
-    fin, lat = 0.0, []
-    for t_a, t_s in zip(arrival, service):
-        fin = max(fin, t_a) + t_s
-        lat.append(fin - t_a)
-    return (len(lat) / fin if fin > 0 else 0.0), lat
+def fifo_replay(arrival, which, call):
+    """The plain path on a trace: one host thread takes the requests in arrival order and serves
+    each with call(pool index), which must finish it (rcm_order_host: host buffers in, result out,
+    synchronous); request k starts when it has arrived and request k-1 has finished. Returns
+    (requests per second over the replay, each request's latency from arrival to finish)."""
+    lat = []
+    t_start = time.perf_counter()
+    for t_a, gi in zip(arrival, which):
+        while time.perf_counter() - t_start < t_a:
+            pass
+        call(int(gi))
+        lat.append(time.perf_counter() - t_start - t_a)
+    t_total = time.perf_counter() - t_start
+    return (len(lat) / t_total if t_total > 0 else 0.0), lat
 
 
 def served_run(args, torch, rcm, setup, options=None, check=True, max_inflight=256):
@@ -342,6 +446,8 @@ def served_run(args, torch, rcm, setup, options=None, check=True, max_inflight=2
             "max_concurrent": info["max_running"], "arena_peak_gb": info["arena_peak_bytes"] / 1e9,
             "fifo_plain_orderings_per_s": setup["fifo_rate"], "fifo_plain_p50_ms": setup["fifo_p50"] * 1e3,
             "fifo_plain_p99_ms": setup["fifo_p99"] * 1e3,
+            "fifo_plain": f"the trace's first {setup['fifo_requests']} requests replayed in real time through "
+                          "rcm_order_host, one at a time in arrival order",
             "vs_fifo_plain": (len(arrival) / t_total) / setup["fifo_rate"], "served_equal_to_plain": same,
             "max_inflight": max_inflight,
             "hardware_queues": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS", "8 (CUDA default)")}
@@ -499,10 +605,10 @@ def main():
                      "bandwidth": qsf["bandwidth_rcm"], "profile": qsf["profile_rcm"], "spmv_ms": qsf["spmv_ms_rcm"],
                      "bandwidth_exact": bw, "profile_exact": prof, "spmv_ms_exact": qual["spmv_ms_rcm"]}
 
-    # roofline of the dominant kernel: the persistent traversal kernel
+    # roofline of the dominant kernel: the persistent traversal kernel, with the bytes the method
+    # needs (one levels-only sweep per sweep but the last, one labelled traversal, the reversal)
     peak, peak_kind = load_peaks()
-    labelled = 1 if stats["traversals"] == stats["sweeps"] else stats["traversals"] - stats["sweeps"] + 1
-    levels_only = stats["traversals"] - labelled
+    levels_only, labelled, _ = method_traversals(stats)
     alg = algorithmic_bytes(n, g.offdiag_nnz(), levels_only, labelled)
     trav = statistics.mean(trav_ms)
     achieved = alg / (trav / 1e3) / 1e9
@@ -510,6 +616,25 @@ def main():
                 "traffic": recorded_traffic("k_rcm_single", f"grid{args.side}"),
                 "kernel": "k_rcm_single", "kernel_ms": trav, "algorithmic_bytes": alg,
                 "peak_kind": f"{peak_kind} hbm_gbs (copy)"}
+
+    # where the kernel's time goes: one more ordering with the per-phase timers on (untimed; CTA 0's
+    # view), and the roofline of the level expansion alone -- the traversal without its grid
+    # exchanges, redistribution and waits
+    po = rcm.rcm_options()
+    ctypes_copy(opts, po)
+    po.profile_phases = 1
+    stp = rcm.rcm_stats()
+    rcm.check(rcm.rcm_order_ex(n, rp, ci, perm, po, stp, stream), "rcm_order_ex")
+    ph = stp.as_dict()["phase_ns"]
+    names = ["levels_only_expansion", "claims", "ownership_and_numbering", "label_writes", "grid_exchanges",
+             "redistribution", "waiting_for_cta0", "start_search_and_resets"]
+    exp_ns = sum(ph[0:4])
+    roofline_expansion = {
+        "bound": "hbm", "achieved": alg / (exp_ns / 1e9) / 1e9 if exp_ns else None, "peak": peak, "unit": "GB/s",
+        "frac": alg / (exp_ns / 1e9) / 1e9 / peak if exp_ns else None, "expansion_ms": exp_ns / 1e6,
+        "kernel_ms_profiled": stp.traverse_ms, "phase_ms": {k: v / 1e6 for k, v in zip(names, ph)},
+        "what": "the same algorithmic bytes over CTA 0's time in the expansion phases (levels-only expansion, "
+                "claims, ownership and numbering, label writes) of one ordering timed with profile_phases = 1"}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -541,6 +666,22 @@ def main():
                "sample": f"{args.cpu_samples} serial orderings of the full workload",
                "ms_per_ordering": statistics.mean(ts) * 1e3}
 
+    # the other single-graph workloads: the 64x64 grid, the 1.2M-point mesh and a 1M-vertex
+    # scale-free graph (hub rows of thousands of entries)
+    configs = None
+    if rank == 0 and not args.no_configs:
+        from paper_1610_08128_gb300 import synth as sy
+
+        configs = {
+            "c1_grid64": bench_config("2D 5-point grid 64x64, ids permuted", sy.c1_grid2d(), args, rcm, torch, flush,
+                                      peak, oracle_orderings=50),
+            "c3_mesh": bench_config("2D kNN(2) mesh of 1.2M points, 1-20 regions (stitched), diagonal stored",
+                                    sy.c3_mesh(), args, rcm, torch, flush, peak),
+            "power_law_1m": bench_config("Chung-Lu power-law graph, 1M vertices, mean degree 10, exponent 2.5",
+                                         sy.power_law(1_000_000, 10, 2.5, sy.SEED_BASE + 6), args, rcm, torch, flush,
+                                         peak),
+        }
+
     batched = served = None
     if not args.no_batched:
         batched = bench_batched(args, torch, rcm, synth_mod, workers, rank, world, dist)
@@ -554,12 +695,12 @@ def main():
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": dict(cfg, parallelism="replicas" if world > 1 else "single", launch=tuned,
                            l2="inputs larger than L2, and a 2x-L2 buffer is written between steps"),
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "roofline_expansion": roofline_expansion, "cpu_baseline": cpu, "e2e": e2e,
             # per step: k_degree_validate, k_sort_rows_small, k_sort_rows_big, k_rcm_single, k_latch
             "gpu_launches": 5 * args.steps, "clocks": clocks,
             "stats": dict(stats, prep_ms=statistics.mean(prep_ms), traverse_ms=trav),
             "quality": dict(qual, bandwidth=bw, profile=prof), "sort_free": sort_free,
-            "batched": batched, "served": served,
+            "configs": configs, "batched": batched, "served": served,
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -70,8 +70,10 @@ typedef struct {
                                   0 = the CTA width                                                 */
     int32_t grid_blocks;       /* CTAs of the persistent grid (<= co-resident limit); 0 = one per SM */
     int32_t block_threads;     /* threads per CTA of the persistent grid: 32 .. 1024 (power of 2); 0 = 512 */
-    int32_t fused_sweeps;      /* 0/1 = label during sweeps 2.. (fused); 2 = label during every sweep,
-                                  the first included; -1 = separate labelled pass                  */
+    int32_t fused_sweeps;      /* 1 = label during sweeps 2.. (fused); 2 = label during every sweep,
+                                  the first included (its labels are discarded); -1 = levels-only
+                                  sweeps, then a separate labelled pass; 0 = 2 on the persistent grid
+                                  (1 with async_sweeps), 1 on the shared-memory CTA. Same result   */
     int64_t spin_limit_ns;     /* bound of every device-side wait; 0 = 20 s                        */
     int64_t nnz;               /* rowptr[n] when the caller knows it: skips the synchronised 4-byte
                                   read (the device still checks it; a mismatch is RCM_ERR_BAD_CSR);
@@ -126,6 +128,14 @@ typedef struct {
                                   (12 bytes per vertex) as persisting in L2, through an access-policy
                                   window; this sets the context's persisting-L2 limit to the window's
                                   size (at most the device maximum). 0 or -1 = off                  */
+    int32_t debug_order_bits;  /* test hook: width of the in-level order field of the labelled
+                                  traversal's 64-bit claim keys; 0 = 64 minus the bits of n + 2 (the
+                                  rest holds the level). The persistent grid runs at most
+                                  floor((2^width - 1) / n) CTAs, so that any CTA's share of a level
+                                  fits the field (the largest graphs run on fewer CTAs; n < 2^31
+                                  always fits on at least one). With a forced width that clamp is
+                                  skipped, and a level share that does not fit ends the call with
+                                  RCM_ERR_TOO_LARGE. 1..(the width from n), else RCM_ERR_INVALID_ARG */
 } rcm_options;
 
 /* Statistics of one ordering (filled by rcm_order_ex when requested). */

@@ -146,9 +146,10 @@ def bandwidth_profile(n, rowptr, colidx, perm, lib=None):
     return int(bw.value), int(prof.value)
 
 
-def rcm_batch(goff, rowptr, colidx, threads: int | None = None, indices=None):
+def rcm_batch(goff, rowptr, colidx, threads: int | None = None, indices=None, with_stats=False):
     """Per-graph oracle orderings of a block-diagonal batch (local ids per segment), one graph per
-    thread (ctypes releases the GIL during the C call). Returns a dict index -> perm."""
+    thread (ctypes releases the GIL during the C call). Returns a dict index -> perm, or index ->
+    (perm, stats) with ``with_stats``."""
     lib = load()
     goff = np.asarray(goff, dtype=np.int64)
     idx = range(len(goff) - 1) if indices is None else indices
@@ -158,7 +159,7 @@ def rcm_batch(goff, rowptr, colidx, threads: int | None = None, indices=None):
         e0, e1 = int(rowptr[a]), int(rowptr[b])
         rp = (rowptr[a:b + 1] - e0).astype(np.int32)
         ci = (colidx[e0:e1] - a).astype(np.int32)
-        return g, rcm(b - a, rp, ci, lib=lib)
+        return g, rcm(b - a, rp, ci, lib=lib, with_stats=with_stats)
 
     threads = threads or len(os.sched_getaffinity(0))
     with ThreadPoolExecutor(max_workers=threads) as ex:

@@ -45,8 +45,13 @@ __global__ void k_batch_validate(int G, int n_total, const long long* __restrict
 
 constexpr int kBatchSortCap = 2048;  // component tables sorted in shared memory up to this size
 
+// CTAs per SM the batched executor is compiled for: many graphs are small, so occupancy matters
+// more than registers (256 threads: 3 per SM at 80 registers measured faster than 4 at 64).
 template <int kThreads>
-__global__ void __launch_bounds__(kThreads) k_rcm_batch(BatchArgs b) {
+constexpr int batch_min_blocks() { return kThreads >= 512 ? 2 : kThreads >= 256 ? 3 : 5; }
+
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_rcm_batch(BatchArgs b) {
     __shared__ EngineSmem smem;
     __shared__ int s_item;
     __shared__ unsigned long long s_sort[kBatchSortCap + kBatchSortCap / 2];

@@ -149,6 +149,7 @@ static rcm_status check_options(const rcm_options* o) {
     if (o->row_order != 0 && o->row_order != 1) return RCM_ERR_INVALID_ARG;
     if (o->expand_mode < 0 || o->expand_mode > 3 || o->bottom_up_divisor < 0) return RCM_ERR_INVALID_ARG;
     if (o->fused_sweeps < -1 || o->fused_sweeps > 2 || o->l2_persist < -1 || o->l2_persist > 1) return RCM_ERR_INVALID_ARG;
+    if (o->debug_order_bits < 0 || o->debug_order_bits > 63) return RCM_ERR_INVALID_ARG;
     return RCM_OK;
 }
 

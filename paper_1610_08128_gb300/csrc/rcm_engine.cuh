@@ -233,6 +233,32 @@ struct Engine {
         r[4] = y.x; r[5] = y.y; r[6] = y.z; r[7] = y.w;
     }
 
+    // ---- long rows, read by the whole warp ----
+    // A row keeps its first kEllNb neighbours in the padded row; the rest (degree > kEllNb) are
+    // read from adj. The lanes holding such a row hand it to the whole warp one row at a time, and
+    // the warp reads it 32 entries per round, coalesced: a hub of a scale-free graph costs its
+    // degree / 32 rounds instead of its degree serial steps in one thread.
+    // fn(src, w) runs on all 32 lanes for one round of lane src's row, w = the lane's entry or -1
+    // past the row's end; it may use warp-collective operations, and returns true (warp-uniform)
+    // to stop reading that row. Must be called by all 32 lanes of the warp.
+    template <class Fn>
+    __device__ void for_long_rows(bool has, int u, int dg, Fn fn) const {
+        unsigned pend = __ballot_sync(0xffffffffu, has && dg > kEllNb);
+        const int lane = threadIdx.x & 31;
+        while (pend) {
+            const int src = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const int uu = __shfl_sync(0xffffffffu, u, src);
+            const int dd = __shfl_sync(0xffffffffu, dg, src);
+            const int* row = a->adj + __ldg(a->rowptr + uu);
+            for (int k0 = kEllNb; k0 < dd; k0 += 32) {
+                const int k = k0 + lane;
+                const int w = k < dd ? __ldg(row + k) : -1;
+                if (fn(src, w)) break;
+            }
+        }
+    }
+
     // Per-thread (count, key) partials: counts go to a shared counter, keys to one slot per warp
     // (a 64-bit shared-memory min would need a compare-and-swap loop). Consumers read the CTA
     // min with cta_key() after a barrier.
@@ -288,7 +314,7 @@ struct Engine {
                     unsigned spins = 0;
                     while ((int)(ld_acquire(&c->arrive) - target) < 0) {
                         if ((++spins & 31u) == 0) {
-                            if (ld_volatile(&c->status) & (kErrTimeout | kErrInternal)) { bad = 1; break; }
+                            if (ld_volatile(&c->status) & (kErrTimeout | kErrInternal | kErrTooLarge)) { bad = 1; break; }
                             if ((long long)(globaltimer_ns() - t0) > a->limit_ns) {
                                 atomicOr(&c->status, kErrTimeout);
                                 bad = 1;
@@ -386,19 +412,26 @@ struct Engine {
                     for (int k = 0; k < kEllNb; ++k) mask |= (old[k] != s ? 1u : 0u) << k;
                 }
             }
-            // overflow neighbours of rows with degree > 7: appended one by one (rare)
-            if (u >= 0 && d > kEllNb) {
-                const int rp = __ldg(a->rowptr + u);
-                for (int k = kEllNb; k < d; ++k) {
-                    const int w = __ldg(a->adj + rp + k);
-                    if (atomicExch(vis_p(w), s) != s) {
-                        const int pos = atomicAdd(tail, 1);
+            // neighbours beyond the padded row (degree > 7), a warp round at a time; the new ones of
+            // a round take consecutive positions reserved by one atomic
+            for_long_rows(u >= 0, u, d, [&](int, int w) {
+                const bool fresh = w >= 0 && atomicExch(vis_p(w), s) != s;
+                const unsigned bal = __ballot_sync(0xffffffffu, fresh);
+                if (bal) {
+                    const int lane = threadIdx.x & 31;
+                    int base = 0;
+                    if (lane == 0) base = atomicAdd(tail, __popc(bal));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (fresh) {
+                        const int pos = base + __popc(bal & ((1u << lane) - 1u));
+                        prefetch_row(w);
                         nxt[pos] = w;
                         if (ncache && pos < kCache) ncache[pos] = w;
-                        ++cnt;
                     }
+                    if (lane == 0) cnt += __popc(bal);
                 }
-            }
+                return false;
+            });
             const int c = __popc(mask);
             int tot;
             const int ex = cta_scan(c, &tot);
@@ -455,6 +488,7 @@ struct Engine {
             const int i = i0 + (int)threadIdx.x;
             const int w = a->v0 + i;
             bool found = false;
+            int dgl = 0;  // degree of an unvisited vertex whose padded row showed no stamped neighbour
             if (i < n && ldcg(vis_p(w)) != s) {
                 int r[8];
                 load_row(w, r);
@@ -464,11 +498,14 @@ struct Engine {
                 for (int k = 0; k < kEllNb; ++k) st[k] = k < dg ? ldcg(vis_p(r[k])) : 0;
 #pragma unroll
                 for (int k = 0; k < kEllNb; ++k) found |= k < dg && st[k] == s;
-                if (!found && dg > kEllNb) {
-                    const int rp = __ldg(a->rowptr + w);
-                    for (int k = kEllNb; k < dg && !found; ++k) found = ldcg(vis_p(__ldg(a->adj + rp + k))) == s;
-                }
+                dgl = found ? 0 : dg;
             }
+            // rows beyond the padded part, by the warp until a stamped neighbour turns up
+            for_long_rows(dgl > kEllNb, w, dgl, [&](int src, int x) {
+                const unsigned bal = __ballot_sync(0xffffffffu, x >= 0 && ldcg(vis_p(x)) == s);
+                if ((int)(threadIdx.x & 31) == src && bal) found = true;
+                return bal != 0;
+            });
             int tot;
             const int ex = cta_scan(found ? 1 : 0, &tot);
             if (tot) {
@@ -572,7 +609,7 @@ struct Engine {
             if (wid == 0) {
                 if (lane == 0) {
                     f = ld_volatile(&ac->flag);
-                    if (ld_volatile(a->status) & (kErrTimeout | kErrInternal)) f |= 4;
+                    if (ld_volatile(a->status) & (kErrTimeout | kErrInternal | kErrTooLarge)) f |= 4;
                     if (!f && (idle & 63) == 0 && (long long)(globaltimer_ns() - t0) > a->limit_ns) {
                         atomicOr(a->status, kErrTimeout);
                         f |= 4;
@@ -938,27 +975,31 @@ struct Engine {
         const int T = blockDim.x, n = a->n;
         const unsigned long long tag = (unsigned long long)(d + 1);
         const int stride = cta_count() * T;
-        for (int i = cta_rank() * T + (int)threadIdx.x; i < n; i += stride) {
+        for (int i0 = cta_rank() * T; i0 < n; i0 += stride) {
+            const int i = i0 + (int)threadIdx.x;
             const int w = a->v0 + i;
-            if (ld_claim(w) != kClaimNone) continue;
-            int r[8];
-            load_row(w, r);
-            const int dg = r[7];
-            unsigned long long kk[kEllNb];
-#pragma unroll
-            for (int k = 0; k < kEllNb; ++k) kk[k] = k < dg ? __ldcg(a->fkey + r[k]) : 0ull;
+            const bool open = i < n && ld_claim(w) == kClaimNone;
             unsigned long long best = kKeyMax;
+            int dg = 0;
+            if (open) {
+                int r[8];
+                load_row(w, r);
+                dg = r[7];
+                unsigned long long kk[kEllNb];
 #pragma unroll
-            for (int k = 0; k < kEllNb; ++k)
-                if ((kk[k] >> a->obits) == tag && kk[k] < best) best = kk[k];
-            if (dg > kEllNb) {
-                const int rp = __ldg(a->rowptr + w);
-                for (int k = kEllNb; k < dg; ++k) {
-                    const unsigned long long x = __ldcg(a->fkey + __ldg(a->adj + rp + k));
-                    if ((x >> a->obits) == tag && x < best) best = x;
-                }
+                for (int k = 0; k < kEllNb; ++k) kk[k] = k < dg ? __ldcg(a->fkey + r[k]) : 0ull;
+#pragma unroll
+                for (int k = 0; k < kEllNb; ++k)
+                    if ((kk[k] >> a->obits) == tag && kk[k] < best) best = kk[k];
             }
-            if (best != kKeyMax) *claim_p(w) = best;
+            for_long_rows(open, w, dg, [&](int src, int x) {
+                unsigned long long v = x >= 0 ? __ldcg(a->fkey + x) : kKeyMax;
+                if ((v >> a->obits) != tag) v = kKeyMax;
+                v = warp_min_u64(v);
+                if ((int)(threadIdx.x & 31) == src && v < best) best = v;
+                return false;
+            });
+            if (open && best != kKeyMax) *claim_p(w) = best;
         }
     }
 
@@ -972,29 +1013,34 @@ struct Engine {
         for (int k = 0; k < 8; ++k) r0[k] = 0;
         for (int j0 = 0; j0 < s.cnt; j0 += T) {
             const int j = j0 + (int)threadIdx.x;
-            if (j >= s.cnt) continue;
-            const int u = sid(s, j);
-            if (!in_graph(u)) {
-                fail(kErrInternal);
-                continue;
-            }
-            int rw[8];
-            load_row(u, rw);
-            const unsigned long long key = level_key(d, ord0 + (unsigned long long)j);
-            const int dg = rw[7];
+            int u = -1, dg = 0;
+            unsigned long long key = 0;
+            if (j < s.cnt) {
+                u = sid(s, j);
+                if (!in_graph(u)) {
+                    fail(kErrInternal);
+                    u = -1;
+                } else {
+                    int rw[8];
+                    load_row(u, rw);
+                    key = level_key(d, ord0 + (unsigned long long)j);
+                    dg = rw[7];
 #pragma unroll
-            for (int k = 0; k < kEllNb; ++k)
-                if (k < dg) atomicMin(claim_p(rw[k]), key);
-            if (dg > kEllNb) {
-                const int rp = __ldg(a->rowptr + u);
-                for (int k = kEllNb; k < dg; ++k) atomicMin(claim_p(__ldg(a->adj + rp + k)), key);
-            }
-            mk = min(mk, pack_key(dg, u));
-            if (j0 == 0) {
-                u0 = u;
+                    for (int k = 0; k < kEllNb; ++k)
+                        if (k < dg) atomicMin(claim_p(rw[k]), key);
+                    mk = min(mk, pack_key(dg, u));
+                    if (j0 == 0) {
+                        u0 = u;
 #pragma unroll
-                for (int k = 0; k < 8; ++k) r0[k] = rw[k];
+                        for (int k = 0; k < 8; ++k) r0[k] = rw[k];
+                    }
+                }
             }
+            for_long_rows(u >= 0, u, dg, [&](int src, int w) {
+                const unsigned long long kk = __shfl_sync(0xffffffffu, key, src);
+                if (w >= 0) atomicMin(claim_p(w), kk);
+                return false;
+            });
         }
         accumulate(0, mk);
     }
@@ -1017,8 +1063,10 @@ struct Engine {
             const int j = j0 + (int)threadIdx.x;
             int c = 0;
             unsigned mask = 0;
+            int u = -1, dg = 0;
+            unsigned long long key = 0;
             if (j < s.cnt) {
-                int u = u0;
+                u = u0;
                 int rw[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) rw[k] = r0[k];
@@ -1027,16 +1075,20 @@ struct Engine {
                     if (in_graph(u)) load_row(u, rw);
                 }
                 if (in_graph(u)) {
-                    const unsigned long long key = level_key(d, ord0 + (unsigned long long)j);
-                    const int dg = rw[7];
+                    key = level_key(d, ord0 + (unsigned long long)j);
+                    dg = rw[7];
                     mask = owned_mask(rw, dg, key);
                     c = __popc(mask);
-                    if (dg > kEllNb) {
-                        const int rp = __ldg(a->rowptr + u);
-                        for (int k = kEllNb; k < dg; ++k) c += (ld_claim(__ldg(a->adj + rp + k)) == key);
-                    }
+                } else {
+                    u = -1;
                 }
             }
+            for_long_rows(u >= 0, u, dg, [&](int src, int w) {
+                const unsigned long long kk = __shfl_sync(0xffffffffu, key, src);
+                const int m = __popc(__ballot_sync(0xffffffffu, w >= 0 && ld_claim(w) == kk));
+                if ((int)(threadIdx.x & 31) == src) c += m;
+                return false;
+            });
             int tot;
             const int ex = cta_scan(c, &tot);
             if (j0 == 0) {
@@ -1061,48 +1113,61 @@ struct Engine {
         // pass 2: write the children
         for (int j0 = 0; j0 < s.cnt; j0 += T) {
             const int j = j0 + (int)threadIdx.x;
-            if (j >= s.cnt) continue;
-            int u = u0;
-            int rw[8];
+            int u = -1, dg = 0, pos = 0;
+            unsigned long long key = 0;
+            if (j < s.cnt) {
+                u = u0;
+                int rw[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) rw[k] = r0[k];
-            unsigned mask = m0;
-            int pos = off0;
-            const unsigned long long key = level_key(d, ord0 + (unsigned long long)j);
-            if (j0 != 0) {
-                u = sid(s, j);
-                if (!in_graph(u)) continue;
-                load_row(u, rw);
-                mask = owned_mask(rw, rw[7], key);
-                pos = a->boff[boff_base + j];
-            }
-            if (!in_graph(u)) continue;
-#pragma unroll
-            for (int k = 0; k < kEllNb; ++k)
-                if (mask & (1u << k)) {
-                    prefetch_row(rw[k]);
-                    dst[pos] = rw[k];
-                    if (lab_base >= 0) {
-                        const int lab = lab_base + pos;
-                        if ((unsigned)lab < (unsigned)n) a->perm[n - 1 - lab] = rw[k]; else fail(kErrInternal);
+                for (int k = 0; k < 8; ++k) rw[k] = r0[k];
+                unsigned mask = m0;
+                pos = off0;
+                key = level_key(d, ord0 + (unsigned long long)j);
+                if (j0 != 0) {
+                    u = sid(s, j);
+                    if (in_graph(u)) {
+                        load_row(u, rw);
+                        mask = owned_mask(rw, rw[7], key);
+                        pos = a->boff[boff_base + j];
                     }
-                    ++pos;
                 }
-            const int dg = rw[7];
-            if (dg > kEllNb) {
-                const int rp = __ldg(a->rowptr + u);
-                for (int k = kEllNb; k < dg; ++k) {
-                    const int w = __ldg(a->adj + rp + k);
-                    if (ld_claim(w) == key) {
-                        dst[pos] = w;
-                        if (lab_base >= 0) {
-                            const int lab = lab_base + pos;
-                            if ((unsigned)lab < (unsigned)n) a->perm[n - 1 - lab] = w; else fail(kErrInternal);
+                if (in_graph(u)) {
+#pragma unroll
+                    for (int k = 0; k < kEllNb; ++k)
+                        if (mask & (1u << k)) {
+                            prefetch_row(rw[k]);
+                            dst[pos] = rw[k];
+                            if (lab_base >= 0) {
+                                const int lab = lab_base + pos;
+                                if ((unsigned)lab < (unsigned)n) a->perm[n - 1 - lab] = rw[k]; else fail(kErrInternal);
+                            }
+                            ++pos;
                         }
-                        ++pos;
-                    }
+                    dg = rw[7];
+                } else {
+                    u = -1;
                 }
             }
+            // the rest of a long row, in row order: a round's owned entries take consecutive
+            // positions after the owner's earlier children
+            for_long_rows(u >= 0, u, dg, [&](int src, int w) {
+                const int lane = threadIdx.x & 31;
+                const unsigned long long kk = __shfl_sync(0xffffffffu, key, src);
+                const bool own = w >= 0 && ld_claim(w) == kk;
+                const unsigned bal = __ballot_sync(0xffffffffu, own);
+                const int base = __shfl_sync(0xffffffffu, pos, src);
+                if (own) {
+                    const int p = base + __popc(bal & ((1u << lane) - 1u));
+                    prefetch_row(w);
+                    dst[p] = w;
+                    if (lab_base >= 0) {
+                        const int lab = lab_base + p;
+                        if ((unsigned)lab < (unsigned)n) a->perm[n - 1 - lab] = w; else fail(kErrInternal);
+                    }
+                }
+                if (lane == src) pos += __popc(bal);
+                return false;
+            });
         }
         __syncthreads();
         return carry;
@@ -1225,6 +1290,12 @@ struct Engine {
                 continue;
             }
             // ---- whole-grid level d: this CTA's slice, ord = b * slot + j ----
+            if ((unsigned long long)cur.cnt > slot) {
+                // the slice's orders would spill into the next CTA's (only with a forced key width:
+                // the host otherwise sizes the grid so that slot >= n); every CTA's next wait sees it
+                fail(kErrTooLarge);
+                return false;
+            }
             const unsigned long long ord0 = (unsigned long long)b * slot;
             int u0;
             int r0[8];
@@ -1457,22 +1528,24 @@ struct Engine {
         }
         if (cta_rank() == 0 && threadIdx.x == 0) *counter = 0;
         if (!barrier()) return -2;
-        for (int i = first; i < n; i += stride) {
+        for (int i0 = cta_rank() * blockDim.x; i0 < n; i0 += stride) {
+            const int i = i0 + (int)threadIdx.x;
             const int v = v0 + i;
-            if (ld_claim(v) != kClaimNone) continue;
-            int r[8];
-            load_row(v, r);
-            const int d = r[7];
+            const bool open = i < n && ld_claim(v) == kClaimNone;
+            int d = 0;
+            if (open) {
+                int r[8];
+                load_row(v, r);
+                d = r[7];
 #pragma unroll
-            for (int k = 0; k < kEllNb; ++k)
-                if (k < d && r[k] < v && !cc_union(a->cc_parent, v, r[k], v0, v0 + n)) fail_at(kSiteParent, v);
-            if (d > kEllNb) {
-                const int rp = __ldg(a->rowptr + v);
-                for (int k = kEllNb; k < d; ++k) {
-                    const int w = __ldg(a->adj + rp + k);
-                    if (w < v && !cc_union(a->cc_parent, v, w, v0, v0 + n)) fail_at(kSiteParent, v);
-                }
+                for (int k = 0; k < kEllNb; ++k)
+                    if (k < d && r[k] < v && !cc_union(a->cc_parent, v, r[k], v0, v0 + n)) fail_at(kSiteParent, v);
             }
+            for_long_rows(open, v, d, [&](int src, int w) {
+                const int vv = __shfl_sync(0xffffffffu, v, src);
+                if (w >= 0 && w < vv && !cc_union(a->cc_parent, vv, w, v0, v0 + n)) fail_at(kSiteParent, vv);
+                return false;
+            });
         }
         if (!barrier()) return -2;
         for (int i = first; i < n; i += stride) {

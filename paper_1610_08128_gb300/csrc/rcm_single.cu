@@ -189,7 +189,7 @@ rcm_status single_launch(int n, long long nnz, const rcm_options& o, SingleLaunc
         sl.by_degree = o.row_order ? 0 : 1;
         sl.threads = t;
         sl.blocks = 1;
-        sl.fused = o.fused_sweeps >= 0 ? 1 : 0;
+        sl.fused = o.fused_sweeps < 0 ? 0 : (o.fused_sweeps == 2 ? 2 : 1);
         sl.profile = o.profile_phases ? 1 : 0;
         *out = sl;
         return RCM_OK;
@@ -218,10 +218,13 @@ rcm_status single_launch(int n, long long nnz, const rcm_options& o, SingleLaunc
         if (sl.blocks < 1 || sl.blocks > max_blocks) return RCM_ERR_INVALID_ARG;
     }
     // claim keys: (level + 1) in the high bits, the in-level order b * slot + j in the low obits;
-    // slot = (2^obits - 1) / blocks must exceed any slice size (< n)
-    const int obits = claim_order_bits(n);
-    const unsigned long long slot_cap = ((1ull << obits) - 1ull) / (unsigned long long)std::max(n, 1);
-    if ((unsigned long long)sl.blocks > slot_cap) {
+    // slot = (2^obits - 1) / blocks must exceed any slice size (< n). A forced width (test hook)
+    // skips the clamp; the kernel then checks every level's slices itself (RCM_ERR_TOO_LARGE).
+    const int natural = claim_order_bits(n);
+    if (o.debug_order_bits > natural) return RCM_ERR_INVALID_ARG;
+    sl.obits = o.debug_order_bits > 0 ? o.debug_order_bits : natural;
+    const unsigned long long slot_cap = ((1ull << sl.obits) - 1ull) / (unsigned long long)std::max(n, 1);
+    if ((unsigned long long)sl.blocks > slot_cap && o.debug_order_bits == 0) {
         if (sl.cluster) return RCM_ERR_TOO_LARGE;
         sl.blocks = (int)std::max(1ull, slot_cap);
     }
@@ -231,7 +234,10 @@ rcm_status single_launch(int n, long long nnz, const rcm_options& o, SingleLaunc
     int narrow = o.narrow_threshold == 0 ? sl.threads : (o.narrow_threshold < 0 ? 0 : o.narrow_threshold);
     sl.narrow = std::min(narrow, kCache);
     sl.limit_ns = o.spin_limit_ns > 0 ? o.spin_limit_ns : 20000000000LL;
-    sl.fused = o.fused_sweeps < 0 ? 0 : (o.fused_sweeps == 2 ? 2 : 1);
+    // label during every sweep by default: on the whole grid a labelled level is cheaper than a
+    // levels-only one (GB300: the 192^3 grid 7.08 against 7.43 ms, a 1000^2 grid 17.7 against
+    // 18.6 ms, the 1.2M-point mesh 24.5 against 25.4 ms). Asynchronous sweeps are levels-only.
+    sl.fused = o.fused_sweeps < 0 ? 0 : o.fused_sweeps == 1 ? 1 : o.fused_sweeps == 2 ? 2 : (sl.async ? 1 : 2);
     sl.profile = o.profile_phases ? 1 : 0;
     sl.stall = o.debug_stall_barrier ? 1 : 0;
     sl.l2_persist = o.l2_persist > 0;
@@ -331,7 +337,7 @@ cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* c
     args.status = &ctl->status;
     args.diag = nullptr;
     args.narrow_thr = sl.narrow;
-    args.obits = claim_order_bits(n);
+    args.obits = sl.obits > 0 ? sl.obits : claim_order_bits(n);
     args.profile = sl.profile;
     args.fused = sl.fused;
     args.limit_ns = sl.limit_ns;

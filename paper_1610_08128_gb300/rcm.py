@@ -46,6 +46,7 @@ class rcm_options(ctypes.Structure):
         ("expand_mode", ctypes.c_int32),
         ("bottom_up_divisor", ctypes.c_int32),
         ("l2_persist", ctypes.c_int32),
+        ("debug_order_bits", ctypes.c_int32),
     ]
 
 

@@ -24,7 +24,7 @@ SINGLE_CANDIDATES = [
     {"executor": 1, "async_sweeps": a, "narrow_threshold": t}
     for a in (1, -1) for t in (128, 256, 512, 1024, 2048)
 ] + [
-    {"executor": 1, "expand_mode": 1, "narrow_threshold": t} for t in (512, 1024)
+    {"executor": 1, "expand_mode": 1, "narrow_threshold": t, "l2_persist": l2} for t in (512, 1024) for l2 in (-1, 1)
 ] + [
     {"executor": 1, "expand_mode": 3, "bottom_up_divisor": dv, "narrow_threshold": t}
     for dv in (4, 16, 64) for t in (512, 1024)

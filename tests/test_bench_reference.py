@@ -47,14 +47,27 @@ def test_bench_launch_options_and_traffic_record():
     assert bench.recorded_traffic("k_rcm_single", "grid7") is None
 
 
-def test_fifo_schedule_of_the_served_baseline():
-    """The FIFO baseline of the served line: one request at a time in arrival order."""
+def test_fifo_replay_of_the_served_baseline():
+    """The FIFO baseline of the served line: the trace replayed in real time, one request at a time
+    in arrival order (a request waits for its arrival and for the one before it)."""
+    import time
+
     sys.path.insert(0, ROOT)
     import bench
 
-    rate, lat = bench.fifo_schedule([0.0, 0.1, 0.15, 5.0], [1.0, 0.5, 0.25, 1.0])
-    # finishes at 1.0, 1.5, 1.75 (queued behind each other), then 6.0 (the server was idle)
-    assert [round(x, 9) for x in lat] == [1.0, 1.4, 1.6, 1.0]
-    assert abs(rate - 4 / 6.0) < 1e-12
-    assert bench.fifo_schedule([], []) == (0.0, [])
+    starts = []
+
+    def call(gi):
+        starts.append((time.perf_counter(), gi))
+        time.sleep(0.05)
+
+    t0 = time.perf_counter()
+    rate, lat = bench.fifo_replay([0.0, 0.01, 0.02, 0.3], [3, 1, 2, 0], call)
+    assert [gi for _, gi in starts] == [3, 1, 2, 0]
+    rel = [t - t0 for t, _ in starts]
+    # the first three queue behind each other; the last waits for its arrival (the server is idle)
+    assert rel[1] >= 0.05 and rel[2] >= 0.10 and rel[3] >= 0.3
+    assert lat[0] >= 0.05 and lat[2] >= 0.13 and 0.05 <= lat[3] < 0.2
+    assert abs(rate - 4 / (rel[3] + 0.05)) < 0.5
+    assert bench.fifo_replay([], [], call) == (0.0, [])
     assert bench.pct([3.0, 1.0, 2.0], 0.5) == 2.0 and bench.pct([], 0.5) is None

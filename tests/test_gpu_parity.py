@@ -202,6 +202,45 @@ def test_rows_stored_in_any_order_every_expansion():
             assert np.array_equal(gpu_perm(g, opts), want), opts
 
 
+def test_power_law_hubs_on_every_executor():
+    """Scale-free patterns whose hub rows hold hundreds to thousands of entries, read by whole warps
+    in every expansion (top-down claims and ownership, bottom-up scans, levels-only sweeps, the
+    union-find of the component pass): the persistent grid in every expansion mode, CTA 0 alone,
+    the asynchronous sweeps, and the shared-memory CTA for a small one."""
+    graphs = [synth.power_law(200000, 10, 2.5, 121), synth.power_law(300000, 6, 2.1, 122)]
+    for g in graphs:
+        want = oracle.rcm(g.n, g.rowptr, g.colidx)
+        for opts in (None, {"executor": 1, "narrow_threshold": -1}, {"expand_mode": 1}, {"expand_mode": 2},
+                     {"expand_mode": 3, "bottom_up_divisor": 64}, {"narrow_threshold": 1 << 30},
+                     {"async_sweeps": 1}, {"fused_sweeps": -1}, {"fused_sweeps": 1}):
+            assert np.array_equal(gpu_perm(g, opts), want), opts
+    for i in range(6):
+        g = synth.power_law(4000, 8, 2.2, [123, i])
+        assert np.diff(g.rowptr).max() > 100
+        assert_parity(g, {"executor": 2})
+        assert_parity(g, {"executor": 1, "narrow_threshold": -1})
+
+
+def test_power_law_batch():
+    """Scale-free graphs in the batched engine (one CTA per graph, long rows read by warps)."""
+    rcm = rcm_mod()
+    graphs = [synth.power_law(int(n), 8, 2.3, [124, i]) for i, n in enumerate([300, 2000, 9000, 30000, 60000])]
+    graphs += [synth.shuffle_rows(g, [125, i]) for i, g in enumerate(graphs)]
+    b = synth.concat(graphs)
+    perm = rcm.order_batch(torch.from_numpy(b.goff).cuda(), torch.from_numpy(b.rowptr).cuda(),
+                           torch.from_numpy(b.colidx).cuda()).cpu().numpy()
+    for gi, g in enumerate(graphs):
+        assert np.array_equal(perm[b.goff[gi]:b.goff[gi + 1]], oracle.rcm(g.n, g.rowptr, g.colidx)), gi
+
+
+@pytest.mark.slow
+def test_power_law_1m_full_size():
+    """A 1,000,000-vertex scale-free graph (hubs of about 7,000 entries), default launch."""
+    g = synth.power_law(1_000_000, 10, 2.5, 5)
+    assert np.diff(g.rowptr).max() > 5000
+    assert_parity(g)
+
+
 @pytest.mark.parametrize("name", ["star41_shuffled.txt", "star41_reversed.txt", "broom78.txt"])
 def test_wide_row_fixtures(name):
     """The hand-worked wide-row fixtures (rows of more than 32 neighbours, stored out of order)."""
@@ -442,6 +481,31 @@ def test_bounded_wait_reports_timeout():
         st = rcm.rcm_stream_status()
     assert st == rcm.RCM_ERR_TIMEOUT
     assert_parity(g)
+
+
+def test_key_order_field_guard():
+    """The labelled traversal's 64-bit claim keys hold the level above an in-level order field
+    ord = b * slot + j; the host sizes the grid so that every CTA's share of a level fits its slot.
+    With the field forced narrow (test hook) the kernel checks the slices itself: a level share that
+    does not fit ends the call with RCM_ERR_TOO_LARGE, no fault, and the context stays usable; a
+    forced width that still fits gives the oracle's order."""
+    rcm = rcm_mod()
+    g = synth.grid((30, 30, 30), seed=131)
+    rp, ci = to_dev(g)
+    perm = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    o = rcm.rcm_options()
+    o.executor, o.narrow_threshold, o.debug_order_bits = 1, -1, 10   # slot = 1023 // CTAs: a few entries
+    st = rcm.rcm_order_ex(g.n, rp, ci, perm, o, None)
+    if st == rcm.RCM_OK:
+        st = rcm.rcm_stream_status()
+    assert st == rcm.RCM_ERR_TOO_LARGE
+    assert_parity(g)
+    o.debug_order_bits = 24                                           # roomy enough: same order
+    rcm.check(rcm.rcm_order_ex(g.n, rp, ci, perm, o, None), "forced width")
+    rcm.check(rcm.rcm_stream_status(), "forced width")
+    assert np.array_equal(perm.cpu().numpy(), oracle.rcm(g.n, g.rowptr, g.colidx))
+    o.debug_order_bits = 63                                           # wider than the level leaves room for
+    assert rcm.rcm_order_ex(g.n, rp, ci, perm, o, None) == rcm.RCM_ERR_INVALID_ARG
 
 
 def test_bandwidth_profile_matches_oracle():
