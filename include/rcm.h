@@ -72,8 +72,9 @@ typedef struct {
     int32_t block_threads;     /* threads per CTA of the persistent grid: 32 .. 1024 (power of 2); 0 = 512 */
     int32_t fused_sweeps;      /* 1 = label during sweeps 2.. (fused); 2 = label during every sweep,
                                   the first included (its labels are discarded); -1 = levels-only
-                                  sweeps, then a separate labelled pass; 0 = 2 on the persistent grid
-                                  (1 with async_sweeps), 1 on the shared-memory CTA. Same result   */
+                                  sweeps, then a separate labelled pass; 0 = 2 on a persistent grid
+                                  of at least 64 CTAs (1 with async_sweeps), 1 on smaller grids,
+                                  clusters and the shared-memory CTA. Same result                  */
     int64_t spin_limit_ns;     /* bound of every device-side wait; 0 = 20 s                        */
     int64_t nnz;               /* rowptr[n] when the caller knows it: skips the synchronised 4-byte
                                   read (the device still checks it; a mismatch is RCM_ERR_BAD_CSR);
@@ -126,8 +127,10 @@ typedef struct {
                                   and at least a quarter of those not yet reached; 0 = 16          */
     int32_t l2_persist;        /* 1 = the persistent grid's launch marks its claim and stamp arrays
                                   (12 bytes per vertex) as persisting in L2, through an access-policy
-                                  window; this sets the context's persisting-L2 limit to the window's
-                                  size (at most the device maximum). 0 or -1 = off                  */
+                                  window; this raises the context's persisting-L2 limit to the
+                                  window's size (at most the device maximum) and keeps it there. A
+                                  small kernel after the traversal turns the window's lines back into
+                                  normal ones, so later work gets the whole L2. 0 or -1 = off       */
     int32_t debug_order_bits;  /* test hook: width of the in-level order field of the labelled
                                   traversal's 64-bit claim keys; 0 = 64 minus the bits of n + 2 (the
                                   rest holds the level). The persistent grid runs at most

@@ -218,12 +218,12 @@ cudaError_t enqueue_batch(int G, long long n_total, int nnz, const long long* go
     const int pb = 256;
     const int pgrid = (int)std::max<long long>(1, std::min<long long>((n_total + pb - 1) / pb, (long long)di.sms * 16));
     // rows longer than small_max entries number at most nnz / (small_max + 1)
-    const int big_grid = (int)std::max<long long>(1, std::min<long long>(2LL * di.sms, nnz / (t.small_max + 1)));
+    const int big_grid = (int)std::max<long long>(1, std::min<long long>(3LL * di.sms, nnz / (t.small_max + 1)));
     if (G > 1) k_batch_validate<<<pgrid, pb, 0, s>>>(G, (int)n_total, goff, rowptr, colidx, ctl);
     k_degree_validate<<<pgrid, pb, 0, s>>>((int)n_total, nnz, rowptr, colidx, deg, claim, vis, big, ctl, t.small_max);
     k_sort_rows_small<<<pgrid, pb, 0, s>>>((int)n_total, rowptr, colidx, deg, adj, ell, ctl, t.small_max,
                                            t.by_degree);
-    k_sort_rows_big<<<big_grid, 1024, sizeof(unsigned long long) * kBigRowSmem, s>>>(
+    k_sort_rows_big<<<big_grid, kBigRowThreads, sizeof(unsigned long long) * kBigRowSmem, s>>>(
         (int)n_total, rowptr, colidx, deg, adj, ell, big, ctl, (unsigned long long*)pool4, t.by_degree);
     BatchArgs b;
     b.G = G;

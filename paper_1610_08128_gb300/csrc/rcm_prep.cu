@@ -61,9 +61,25 @@ __global__ void k_sort_rows_small(int n, const int* __restrict__ rowptr, const i
         if (rowptr[v + 1] - rowptr[v] <= small_max) sort_small_row(v, rowptr, colidx, deg, adj, ell, by_degree);
 }
 
-// Rows longer than the per-thread sorter: one CTA per row, bitonic sort in shared memory for rows
-// of at most kBigRowSmem entries; longer rows are sorted by CTA 0 alone in global scratch
-// (scratch holds next_pow2(maxdeg) keys).
+// Sorted row of v from keys[0, m) already sorted: the full row into adj (from offset a) and the
+// padded row (first 7 + degree); one thread writes the padded row.
+__device__ __forceinline__ void write_sorted_row(int v, int a, int m, const unsigned long long* keys, int* adj,
+                                                 int4* ell, int t, int nt) {
+    for (int i = t; i < m; i += nt) adj[a + i] = (int)(unsigned)(keys[i] & 0xffffffffu);
+    if (t == 0) {
+        int r[8];
+        for (int i = 0; i < 7; ++i) r[i] = i < m ? (int)(unsigned)(keys[i] & 0xffffffffu) : -1;
+        r[7] = m;
+        store_ell(ell, v, r);
+    }
+}
+
+// Rows longer than the per-thread sorter (listed in bigrows), by size:
+//   at most kWarpRowMax entries: one warp per row, bitonic sort in the warp's slice of shared memory
+//     (the rows of scale-free graphs are mostly a few dozen entries long);
+//   at most kBigRowSmem keys: one CTA per row, bitonic sort in shared memory;
+//   longer: CTA 0 alone, in global scratch (scratch holds next_pow2(maxdeg) keys).
+// Launched with kBigRowThreads threads and kBigRowSmem keys of dynamic shared memory.
 __global__ void k_sort_rows_big(int n, const int* __restrict__ rowptr, const int* __restrict__ colidx,
                                 const int* __restrict__ deg, int* __restrict__ adj, int4* __restrict__ ell,
                                 const int* __restrict__ bigrows, const Ctl* ctl,
@@ -72,43 +88,73 @@ __global__ void k_sort_rows_big(int n, const int* __restrict__ rowptr, const int
     __shared__ int s_m;
     if (ctl->status & kErrBadCsr) return;
     const int nbig = ctl->nbig;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // one warp per row; the keys are gathered in stored order (a warp compaction skips the diagonal)
+    unsigned long long* ws = s_keys + (size_t)wid * kWarpRowMax;
+    for (int r = blockIdx.x * nw + wid; r < nbig; r += gridDim.x * nw) {
+        const int v = bigrows[r];
+        const int a = rowptr[v], b = rowptr[v + 1];
+        if (b - a > kWarpRowMax) continue;
+        int m = 0;
+        for (int k0 = a; k0 < b; k0 += 32) {
+            const int k = k0 + lane;
+            const int w = k < b ? colidx[k] : v;
+            const bool keep = w != v;
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (keep) ws[m + __popc(bal & ((1u << lane) - 1u))] = row_key(deg, w, k - a, by_degree);
+            m += __popc(bal);
+        }
+        int P = 1;
+        while (P < m) P <<= 1;
+        for (int i = m + lane; i < P; i += 32) ws[i] = kKeyMax;
+        __syncwarp();
+        bitonic_sort_warp(ws, P);
+        write_sorted_row(v, a, m, ws, adj, ell, lane, 32);
+        __syncwarp();
+    }
+    __syncthreads();
+    // one CTA per row
     for (int r = blockIdx.x; r < nbig; r += gridDim.x) {
         const int v = bigrows[r];
         const int a = rowptr[v], b = rowptr[v + 1];
+        if (b - a <= kWarpRowMax) continue;
         const int m = deg[v];
         int P = 1;
         while (P < m) P <<= 1;
-        const bool in_smem = P <= kBigRowSmem;
-        if (!in_smem && blockIdx.x != 0) continue;
-        unsigned long long* s = in_smem ? s_keys : scratch;
+        if (P > kBigRowSmem) continue;
         if (threadIdx.x == 0) s_m = 0;
         __syncthreads();
         for (int k = a + threadIdx.x; k < b; k += blockDim.x) {
             const int w = colidx[k];
-            if (w != v) s[atomicAdd(&s_m, 1)] = row_key(deg, w, k - a, by_degree);
+            if (w != v) s_keys[atomicAdd(&s_m, 1)] = row_key(deg, w, k - a, by_degree);
         }
         __syncthreads();
-        for (int i = m + threadIdx.x; i < P; i += blockDim.x) s[i] = kKeyMax;
+        for (int i = m + threadIdx.x; i < P; i += blockDim.x) s_keys[i] = kKeyMax;
         __syncthreads();
-        bitonic_sort_cta(s, P);
-        for (int i = threadIdx.x; i < m; i += blockDim.x) adj[a + i] = (int)(unsigned)(s[i] & 0xffffffffu);
-        if (threadIdx.x == 0) {
-            int r[8];
-            for (int i = 0; i < 7; ++i) r[i] = i < m ? (int)(unsigned)(s[i] & 0xffffffffu) : -1;
-            r[7] = m;
-            store_ell(ell, v, r);
-        }
+        bitonic_sort_cta(s_keys, P);
+        write_sorted_row(v, a, m, s_keys, adj, ell, threadIdx.x, blockDim.x);
         __syncthreads();
     }
-    // Huge rows assigned to other CTAs by the stride are picked up here by CTA 0.
+    // rows beyond shared memory, by CTA 0 in global scratch: its threads scan the list together
+    // (one entry each per round), then sort the rows found one after another
     if (blockIdx.x != 0) return;
-    for (int r = 0; r < nbig; ++r) {
-        if (r % gridDim.x == 0) continue;  // already handled above by CTA 0
-        const int v = bigrows[r];
+    for (int r0 = 0; r0 < nbig; r0 += blockDim.x) {
+        const int r = r0 + (int)threadIdx.x;
+        const bool huge = r < nbig && deg[bigrows[r]] > kBigRowSmem;
+        const int cnt = __syncthreads_count(huge);
+        if (cnt == 0) continue;
+        if (threadIdx.x == 0) s_m = kIntMax;
+        __syncthreads();
+        if (huge) atomicMin(&s_m, r);
+        __syncthreads();
+        // sort the first huge row of this round, then rescan from just after it
+        const int rr = s_m;
+        __syncthreads();
+        r0 = rr + 1 - (int)blockDim.x;
+        const int v = bigrows[rr];
         const int m = deg[v];
         int P = 1;
         while (P < m) P <<= 1;
-        if (P <= kBigRowSmem) continue;
         const int a = rowptr[v], b = rowptr[v + 1];
         if (threadIdx.x == 0) s_m = 0;
         __syncthreads();
@@ -120,13 +166,7 @@ __global__ void k_sort_rows_big(int n, const int* __restrict__ rowptr, const int
         for (int i = m + threadIdx.x; i < P; i += blockDim.x) scratch[i] = kKeyMax;
         __syncthreads();
         bitonic_sort_cta(scratch, P);
-        for (int i = threadIdx.x; i < m; i += blockDim.x) adj[a + i] = (int)(unsigned)(scratch[i] & 0xffffffffu);
-        if (threadIdx.x == 0) {
-            int r[8];
-            for (int i = 0; i < 7; ++i) r[i] = i < m ? (int)(unsigned)(scratch[i] & 0xffffffffu) : -1;
-            r[7] = m;
-            store_ell(ell, v, r);
-        }
+        write_sorted_row(v, a, m, scratch, adj, ell, threadIdx.x, blockDim.x);
         __syncthreads();
     }
 }

@@ -7,6 +7,8 @@ namespace rcm {
 
 constexpr int kSmallRowMax = 32;     // rows with at most this many stored entries: per-thread sort
 constexpr int kBigRowSmem = 8192;    // rows sorted in shared memory by one CTA (64 KB of keys)
+constexpr int kBigRowThreads = 256;  // CTA width of k_sort_rows_big: 8 warps
+constexpr int kWarpRowMax = kBigRowSmem / (kBigRowThreads / 32);  // rows sorted by one warp (its 8 KB slice)
 
 // Padded row of vertex v: its first 7 neighbours in (degree, id) order (-1 where absent) and its
 // degree in slot 7, as two 16-byte stores (one 32-byte sector per vertex).
@@ -31,6 +33,27 @@ __device__ __forceinline__ void bitonic_sort_cta(unsigned long long* s, int P) {
                 }
             }
             __syncthreads();
+        }
+    }
+}
+
+// Bitonic sort of P (a power of two, at most kWarpRowMax) keys in `s` by one warp.
+__device__ __forceinline__ void bitonic_sort_warp(unsigned long long* s, int P) {
+    const int lane = threadIdx.x & 31;
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < P; i += 32) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const bool asc = (i & k) == 0;
+                    unsigned long long x = s[i], y = s[ixj];
+                    if ((x > y) == asc) {
+                        s[i] = y;
+                        s[ixj] = x;
+                    }
+                }
+            }
+            __syncwarp();
         }
     }
 }

@@ -19,6 +19,9 @@ namespace rcm {
 // CTA each, concurrently.
 constexpr int kComponentOnGrid = 1 << 18;
 
+// Grids of at least this many CTAs label during every sweep by default (see single_launch).
+constexpr int kLabelEverySweepBlocks = 64;
+
 // with_cc: also the arrays of the concurrent-components pass (the fixed no-allocation workspace
 // leaves them out and orders components one by one).
 SingleLayout single_layout(long long n, long long nnz, bool with_cc, bool with_async, bool with_fkey) {
@@ -234,10 +237,13 @@ rcm_status single_launch(int n, long long nnz, const rcm_options& o, SingleLaunc
     int narrow = o.narrow_threshold == 0 ? sl.threads : (o.narrow_threshold < 0 ? 0 : o.narrow_threshold);
     sl.narrow = std::min(narrow, kCache);
     sl.limit_ns = o.spin_limit_ns > 0 ? o.spin_limit_ns : 20000000000LL;
-    // label during every sweep by default: on the whole grid a labelled level is cheaper than a
-    // levels-only one (GB300: the 192^3 grid 7.08 against 7.43 ms, a 1000^2 grid 17.7 against
-    // 18.6 ms, the 1.2M-point mesh 24.5 against 25.4 ms). Asynchronous sweeps are levels-only.
-    sl.fused = o.fused_sweeps < 0 ? 0 : o.fused_sweeps == 1 ? 1 : o.fused_sweeps == 2 ? 2 : (sl.async ? 1 : 2);
+    // label during every sweep by default on a wide grid: there a labelled level is cheaper than a
+    // levels-only one (GB300, 152 CTAs: the 192^3 grid 7.08 against 7.43 ms, a 1000^2 grid 17.7
+    // against 18.6 ms, the 1.2M-point mesh 24.5 against 25.4 ms). On a few CTAs the extra work of
+    // a labelled first sweep costs more than it saves (one cluster of 6: a 100^3 grid 8.6 against
+    // 6.8 ms). Asynchronous sweeps are levels-only.
+    sl.fused = o.fused_sweeps < 0 ? 0 : o.fused_sweeps == 1 ? 1 : o.fused_sweeps == 2 ? 2
+             : (sl.async || sl.blocks < kLabelEverySweepBlocks) ? 1 : 2;
     sl.profile = o.profile_phases ? 1 : 0;
     sl.stall = o.debug_stall_barrier ? 1 : 0;
     sl.l2_persist = o.l2_persist > 0;
@@ -285,6 +291,43 @@ static cudaError_t launch_persisting(const void* kernel, const SingleLaunch& sl,
     return cudaLaunchKernelExC(&cfg, kernel, kargs);
 }
 
+// Reads one word of every 128-byte line of [p, p + words): launched with a normal-access window
+// over the range, it turns the lines that a persisting window left in L2 back into normal ones,
+// so that later kernels of the caller get the whole L2 again.
+__global__ void k_l2_release(const int* __restrict__ p, size_t words) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x * 32;
+    for (size_t i = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 32; i < words; i += stride) {
+        int x;
+        asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(x) : "l"(p + i) : "memory");
+    }
+}
+
+static cudaError_t release_persisting(const char* win, size_t bytes, cudaStream_t s) {
+    int dev = 0, max_window = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev);
+    if (e != cudaSuccess) return e;
+    const size_t window = std::min(bytes, (size_t)max_window);
+    const size_t words = window / sizeof(int);
+    const DeviceInfo& di = device_info();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::max<size_t>(1, std::min<size_t>((words / 32 + 255) / 256, (size_t)di.sms * 8)));
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    attr[0].val.accessPolicyWindow.base_ptr = (void*)win;
+    attr[0].val.accessPolicyWindow.num_bytes = window;
+    attr[0].val.accessPolicyWindow.hitRatio = 1.0f;
+    attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyNormal;
+    attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyNormal;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const int* p = (const int*)win;
+    void* kargs[] = {(void*)&p, (void*)&words};
+    return cudaLaunchKernelExC(&cfg, (const void*)k_l2_release, kargs);
+}
+
 cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* colidx, int* perm, char* base,
                            const SingleLayout& L, const SingleLaunch& sl, cudaEvent_t* ev, cudaStream_t s) {
     const DeviceInfo& di = device_info();
@@ -313,8 +356,8 @@ cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* c
         k_sort_rows_small<<<std::max(pgrid, 1), pb, 0, s>>>(n, rowptr, colidx, deg, adj, ell, ctl, kSmallRowMax,
                                                            sl.by_degree);
         // rows longer than kSmallRowMax entries number at most nnz / (kSmallRowMax + 1)
-        const int big_grid = (int)std::max<long long>(1, std::min<long long>(2LL * di.sms, nnz / (kSmallRowMax + 1)));
-        k_sort_rows_big<<<big_grid, 1024, sizeof(unsigned long long) * kBigRowSmem, s>>>(
+        const int big_grid = (int)std::max<long long>(1, std::min<long long>(3LL * di.sms, nnz / (kSmallRowMax + 1)));
+        k_sort_rows_big<<<big_grid, kBigRowThreads, sizeof(unsigned long long) * kBigRowSmem, s>>>(
             n, rowptr, colidx, deg, adj, ell, bigrows, ctl, (unsigned long long*)pool4, sl.by_degree);
         e = cudaGetLastError();
         if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
@@ -390,6 +433,9 @@ cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* c
     } else if (sl.l2_persist) {
         e = launch_persisting(single_kernel(sl.threads, async, hybrid), sl, kargs, base + L.claim,
                               L.bigrows - L.claim, s);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
+        if (e == cudaSuccess) e = release_persisting(base + L.claim, L.bigrows - L.claim, s);
+        return e;
     } else {
         e = cudaLaunchCooperativeKernel(single_kernel(sl.threads, async, hybrid), dim3(sl.blocks), dim3(sl.threads), kargs,
                                         kSingleDynSmem, s);

@@ -26,6 +26,26 @@ def shard_by_size(sizes, world: int) -> list[list[int]]:
     return [sorted(s) for s in shards]
 
 
+def assemble(parts, count: int) -> list:
+    """Per-graph results of all ranks back in the original order: parts holds one mapping
+    {graph index: result} per rank (each rank ordered its shard). Raises if a graph is missing or
+    was returned by more than one rank."""
+    out = [None] * count
+    seen = [False] * count
+    for part in parts:
+        for i, res in part.items():
+            if not 0 <= i < count:
+                raise ValueError(f"graph index {i} outside the batch of {count}")
+            if seen[i]:
+                raise ValueError(f"graph {i} returned by more than one rank")
+            seen[i] = True
+            out[i] = res
+    missing = [i for i in range(count) if not seen[i]]
+    if missing:
+        raise ValueError(f"{len(missing)} graphs returned by no rank, first {missing[:5]}")
+    return out
+
+
 def max_over_ranks(value: float, dist=None, device=None) -> float:
     """The largest `value` over all ranks (the job takes as long as its slowest rank)."""
     if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:

@@ -465,12 +465,21 @@ def default_workers() -> int:
     return max(1, min(32, len(os.sched_getaffinity(0))))
 
 
-def c4_batch(G: int = 10_000, nmin: int = 100, nmax: int = 50_000, seed_offset: int = 0, workers: int = 1) -> Batch:
-    """G independent graphs, vertex counts log-uniform in [nmin, nmax], kind uniform over
-    {2D grid, 3D grid, kNN(3) mesh}, ids permuted per graph, concatenated block-diagonally."""
+def c4_specs(G: int = 10_000, nmin: int = 100, nmax: int = 50_000, seed_offset: int = 0):
+    """The (kind, n, seed) of every graph of the batched workload, without building any."""
     base = SEED_BASE + 4 + 1000 * seed_offset
     sizes, kinds = mix_sizes(G, nmin, nmax, base)
-    specs = [(int(k), int(s), [base, i]) for i, (k, s) in enumerate(zip(kinds, sizes))]
+    return [(int(k), int(s), [base, i]) for i, (k, s) in enumerate(zip(kinds, sizes))]
+
+
+def c4_batch(G: int = 10_000, nmin: int = 100, nmax: int = 50_000, seed_offset: int = 0, workers: int = 1,
+             indices=None) -> Batch:
+    """G independent graphs, vertex counts log-uniform in [nmin, nmax], kind uniform over
+    {2D grid, 3D grid, kNN(3) mesh}, ids permuted per graph, concatenated block-diagonally.
+    With ``indices``, only those graphs of the G (in that order): one rank's share of the batch."""
+    specs = c4_specs(G, nmin, nmax, seed_offset)
+    if indices is not None:
+        specs = [specs[i] for i in indices]
     return concat(make_graphs(specs, workers))
 
 

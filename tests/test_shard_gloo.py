@@ -74,3 +74,58 @@ def test_two_gloo_ranks_shard_and_reduce():
     assert not set(mine0) & set(mine1)
     assert res[0][2] == res[1][2] == 2.0              # max over ranks of (1 + rank)
     assert res[0][3] == res[1][3] == float(np.sum(sizes))
+
+
+def _batch_worker(rank, world, port, G, out):
+    """One rank: its size-balanced share of a batch, ordered on the host by the oracle (the GPU
+    runs order it with rcm_order_batch), results gathered for reassembly."""
+    import torch.distributed as dist
+
+    import oracle
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        specs = synth.c4_specs(G, 20, 400)
+        mine = shard.shard_by_size([n for _, n, _ in specs], world)[rank]
+        b = synth.c4_batch(G, 20, 400, indices=mine)
+        perms = oracle.rcm_batch(b.goff, b.rowptr, b.colidx, threads=2)
+        part = {gi: perms[k].tolist() for k, gi in enumerate(mine)}
+        parts = [None] * world
+        dist.all_gather_object(parts, part)
+        out.put((rank, mine, parts))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_order_one_batch_split_by_size():
+    """One batch partitioned by size over two ranks, each ordering only its own graphs; the
+    gathered per-graph results reassemble into the whole batch, every graph once and in the
+    original order, equal to ordering the unsplit batch."""
+    import multiprocessing as mp
+
+    import oracle
+
+    G = 40
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_batch_worker, args=(r, 2, port, G, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=180) for _ in procs), key=lambda x: x[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res[0][2] == res[1][2]                      # both ranks gathered the same parts
+    assert sorted(res[0][1] + res[1][1]) == list(range(G)) and res[0][1] and res[1][1]
+    whole = shard.assemble(res[0][2], G)
+    full = synth.c4_batch(G, 20, 400)
+    ref = oracle.rcm_batch(full.goff, full.rowptr, full.colidx, threads=2)
+    for gi in range(G):
+        assert whole[gi] == ref[gi].tolist(), gi
+    with pytest.raises(ValueError):
+        shard.assemble([{0: 1}, {0: 1}], 1)              # a graph from two ranks
+    with pytest.raises(ValueError):
+        shard.assemble([{0: 1}], 2)                      # a graph from none
