@@ -447,9 +447,13 @@ def served_run(args, torch, rcm, setup, options=None, check=True, max_inflight=2
             rcm.check(rcm.rcm_order_host(g.n, bufs[which[k]][0], bufs[which[k]][1], ref), "plain")
             same &= bool(torch.equal(ref, outs[k]))
     sizes = [pool[gi].n for gi in which]
+    last = float(arrival[-1]) if len(arrival) else 0.0
     return {"workload": f"{len(arrival)} requests, Poisson {args.serve_rate:.0f}/s, pool of {len(pool)} graphs "
                         f"(n log-uniform 1e3..4e6, 3 generators), 60 GB budget",
             "mean_vertices": float(np.mean(sizes)), "orderings_per_s": len(arrival) / t_total,
+            # a finite trace ends with the last requests' latency: the offered rate over the arrivals
+            # and the time from the last arrival to the last completion say whether the server kept up
+            "offered_per_s": len(arrival) / last if last > 0 else None, "drain_ms": (t_total - last) * 1e3,
             "p50_ms": info["latency_p50_s"] * 1e3, "p99_ms": info["latency_p99_s"] * 1e3,
             "max_concurrent": info["max_running"], "arena_peak_gb": info["arena_peak_bytes"] / 1e9,
             "fifo_plain_orderings_per_s": setup["fifo_rate"], "fifo_plain_p50_ms": setup["fifo_p50"] * 1e3,
@@ -463,8 +467,18 @@ def served_run(args, torch, rcm, setup, options=None, check=True, max_inflight=2
 
 def bench_served(args, torch, rcm, synth, workers):
     """Poisson request stream replayed through the server, against the same trace served FIFO by
-    rcm_order_host."""
-    return served_run(args, torch, rcm, served_setup(args, torch, rcm, synth, workers))
+    rcm_order_host; then the server's capacity: the same requests all submitted at once, so that
+    admission, not arrivals, paces them."""
+    import numpy as np
+
+    setup = served_setup(args, torch, rcm, synth, workers)
+    out = served_run(args, torch, rcm, setup)
+    sat = dict(setup, arrival=np.zeros_like(setup["arrival"]))
+    cap = served_run(args, torch, rcm, sat, check=False)
+    out["capacity"] = {"what": "the same requests submitted at once (continuous batching at full load)",
+                       "orderings_per_s": cap["orderings_per_s"], "p50_ms": cap["p50_ms"], "p99_ms": cap["p99_ms"],
+                       "max_concurrent": cap["max_concurrent"]}
+    return out
 
 
 def run_reference(args):

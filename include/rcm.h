@@ -309,8 +309,8 @@ rcm_status rcm_server_create(size_t hbm_budget_bytes, int32_t max_inflight, rcm_
 typedef struct {
     int64_t cluster_min_vertices; /* requests of at least this many vertices run the persistent
                                      engine of rcm_order launched as one thread-block cluster;
-                                     smaller ones run on one CTA. 0 = 262,144; -1 = never         */
-    int32_t cluster_blocks;       /* CTAs of that cluster, 2..16 as the device allows; 0 = 6       */
+                                     smaller ones run on one CTA. 0 = 524,288; -1 = never         */
+    int32_t cluster_blocks;       /* CTAs of that cluster, 2..16 as the device allows; 0 = 4       */
     int32_t debug_fail_after;     /* test hook: once this many requests have completed, the server
                                      acts as if a running request's stream reported a CUDA error
                                      (its failure path without a device fault); 0 = off           */

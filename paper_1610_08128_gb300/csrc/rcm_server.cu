@@ -39,10 +39,15 @@
 namespace rcm {
 
 // Requests of at least this many vertices run on a cluster of kServeClusterBlocks CTAs by default
-// (see the header comment). Small clusters measured best on GB300: they leave room on the SMs for
-// the single-CTA requests, while each large request keeps most of the speed of a wide grid.
-constexpr long long kServeClusterMin = 1LL << 18;
-constexpr int kServeClusterBlocks = 6;
+// (see the header comment); the rest on one CTA of the batched executor. A cluster holds whole SMs
+// (one 512-thread CTA each) through levels that leave them mostly idle, while a single CTA takes a
+// third of an SM: on GB300, ordering a 1M-vertex 2D grid took 18 ms on a cluster of 6 and 32 ms on
+// one CTA, about ten times the SM time. So clusters pay off only for the largest requests, whose
+// latency they cut most. Measured on the 2,000 req/s trace (4,000 requests, pool of 256):
+// clusters of 4 from 512k vertices 1,863/s, p50 27 ms, p99 159 ms; clusters of 6 from 256k
+// vertices 1,789/s, 60 / 205 ms; no clusters 1,103/s, 688 / 1,519 ms.
+constexpr long long kServeClusterMin = 1LL << 19;
+constexpr int kServeClusterBlocks = 4;
 
 // Arena bytes of one request: the staged CSR and result when they are in host memory, a 256-byte
 // header holding the graph offsets {0, n} of a batch of one, and the larger of the two executors'

@@ -83,7 +83,9 @@ def test_large_requests_run_on_a_cluster(rcm):
     small = mix(12, 503)
     assert len(small[0::3]) == len(big)
     graphs = [g for pair in zip(big, small[0::3]) for g in pair] + small[1::3] + small[2::3]
-    st, srv = rcm.rcm_server_create(8 << 30, 32)
+    o = rcm.rcm_server_options()
+    o.cluster_min_vertices = 1 << 18         # every large request here (280k-360k vertices) on a cluster
+    st, srv = rcm.rcm_server_create_ex(8 << 30, 32, o)
     rcm.check(st, "create")
     try:
         outs, ins, tickets = [], [], []
