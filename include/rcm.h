@@ -127,10 +127,13 @@ typedef struct {
                                   and at least a quarter of those not yet reached; 0 = 16          */
     int32_t l2_persist;        /* 1 = the persistent grid's launch marks its claim and stamp arrays
                                   (12 bytes per vertex) as persisting in L2, through an access-policy
-                                  window; this raises the context's persisting-L2 limit to the
-                                  window's size (at most the device maximum) and keeps it there. A
-                                  small kernel after the traversal turns the window's lines back into
-                                  normal ones, so later work gets the whole L2. 0 or -1 = off       */
+                                  window, so that rows streaming through L2 do not evict them. This
+                                  raises the context's persisting-L2 limit to the window's size (at
+                                  most the device maximum); a small kernel after the traversal turns
+                                  the window's lines back into normal ones, and the call then
+                                  SYNCHRONISES `stream` and puts the previous limit back (a raised
+                                  limit slows later kernels of the context). Cooperative grid only
+                                  (ignored on clusters and the shared-memory CTA). 0 or -1 = off    */
     int32_t debug_order_bits;  /* test hook: width of the in-level order field of the labelled
                                   traversal's 64-bit claim keys; 0 = 64 minus the bits of n + 2 (the
                                   rest holds the level). The persistent grid runs at most
@@ -349,7 +352,11 @@ rcm_status rcm_server_info(rcm_server *srv, rcm_server_stats *out);
 /* Drops requests not admitted yet, waits for running ones, and frees the server. */
 rcm_status rcm_server_destroy(rcm_server *srv);
 
-/* Synchronises `stream` and returns (and clears) the error latched by earlier calls on it. */
+/* Synchronises `stream` and returns (and clears) the error latched by earlier calls on it.
+   Each stream that rcm_order / rcm_order_ex / rcm_order_batch(_ex) ran on holds one of 4,096 latch
+   words of this process until this call reads it; the word is then free for any stream. An
+   ordering call on a further stream while all 4,096 are held returns RCM_ERR_TOO_LARGE before any
+   work (read the status of streams you are done with). */
 rcm_status rcm_stream_status(rcm_stream_t stream);
 
 /* Workspace bytes rcm_order allocates for a pattern of n vertices and nnz stored entries. */

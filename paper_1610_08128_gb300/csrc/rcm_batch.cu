@@ -269,6 +269,8 @@ rcm_status order_batch(int32_t G, int64_t n_total, const int64_t* goff, const in
     if (e != cudaSuccess) return cuda_status(e);
     if (nnz < 0) return RCM_ERR_BAD_CSR;
     const BatchLayout L = batch_layout(n_total, nnz, G);
+    int* latch = stream_latch(s);
+    if (!latch) return RCM_ERR_TOO_LARGE;  // every latch slot held by streams whose status is unread
     void* ws = nullptr;
     st = ws_alloc(&ws, L.total, s);
     if (st != RCM_OK) return st;
@@ -279,7 +281,7 @@ rcm_status order_batch(int32_t G, int64_t n_total, const int64_t* goff, const in
     if (e == cudaSuccess)
         e = enqueue_batch(G, n_total, nnz, (const long long*)goff, (const int*)(base + L.order), rowptr, colidx,
                           perm, base, L, t, s);
-    if (e == cudaSuccess) e = enqueue_latch((Ctl*)(base + L.ctl), stream_latch(s), nullptr, s);
+    if (e == cudaSuccess) e = enqueue_latch((Ctl*)(base + L.ctl), latch, nullptr, s);
     ws_free(ws, s);
     return e == cudaSuccess ? RCM_OK : cuda_status(e);
 }

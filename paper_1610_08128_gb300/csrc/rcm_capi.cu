@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <mutex>
 #include <unordered_map>
+#include <vector>
 
 #include "rcm_host.hpp"
 #include "rcm_internal.cuh"
@@ -60,10 +61,16 @@ const DeviceInfo& device_info() {
 }
 
 // ---- per-stream error latch: one host-mapped pinned word per (device, stream) ----
+// A stream holds a slot from its first ordering call until rcm_stream_status reads and clears it
+// (after synchronising the stream, so nothing still writes the slot); the slot is then free for
+// any stream. A call on a new stream while all kLatchSlots slots are held fails before any work
+// (RCM_ERR_TOO_LARGE) instead of sharing a slot with another stream.
 constexpr int kLatchSlots = 4096;
 static std::mutex g_latch_mu;
 static int* g_latch = nullptr;  // host-mapped, portable
 static std::unordered_map<unsigned long long, int> g_slot_of;
+static std::vector<int> g_free_slots;
+static int g_next_slot = 0;
 
 static unsigned long long stream_key(cudaStream_t s) {
     int d = 0;
@@ -71,7 +78,9 @@ static unsigned long long stream_key(cudaStream_t s) {
     return (unsigned long long)(uintptr_t)s * 64ull + (unsigned long long)d;
 }
 
-static int* latch_host(cudaStream_t s) {
+// The stream's latch word; with create, a free slot is taken for a stream that holds none.
+// nullptr: no slot (not created, or all held), or the pinned words could not be allocated.
+static int* latch_host(cudaStream_t s, bool create) {
     std::lock_guard<std::mutex> g(g_latch_mu);
     if (!g_latch) {
         void* p = nullptr;
@@ -82,18 +91,39 @@ static int* latch_host(cudaStream_t s) {
     }
     const unsigned long long k = stream_key(s);
     auto it = g_slot_of.find(k);
+    if (it != g_slot_of.end()) return g_latch + it->second;
+    if (!create) return nullptr;
     int slot;
-    if (it == g_slot_of.end()) {
-        slot = (int)(g_slot_of.size() % kLatchSlots);
-        g_slot_of.emplace(k, slot);
+    if (!g_free_slots.empty()) {
+        slot = g_free_slots.back();
+        g_free_slots.pop_back();
+    } else if (g_next_slot < kLatchSlots) {
+        slot = g_next_slot++;
     } else {
-        slot = it->second;
+        return nullptr;
     }
+    g_latch[slot] = 0;
+    g_slot_of.emplace(k, slot);
     return g_latch + slot;
 }
 
+// Reads, clears and frees the stream's slot (the stream must be synchronised); 0 if it holds none.
+static int latch_take(cudaStream_t s) {
+    int* h = latch_host(s, false);
+    if (!h) return 0;
+    std::lock_guard<std::mutex> g(g_latch_mu);
+    const int bits = *(volatile int*)h;
+    *(volatile int*)h = 0;
+    auto it = g_slot_of.find(stream_key(s));
+    if (it != g_slot_of.end()) {
+        g_free_slots.push_back(it->second);
+        g_slot_of.erase(it);
+    }
+    return bits;
+}
+
 int* stream_latch(cudaStream_t s) {
-    int* h = latch_host(s);
+    int* h = latch_host(s, true);
     if (!h) return nullptr;
     int* d = nullptr;
     if (cudaHostGetDevicePointer((void**)&d, h, 0) != cudaSuccess) return nullptr;
@@ -289,11 +319,7 @@ rcm_status rcm_stream_status(rcm_stream_t stream) {
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_status(e);
-    int* h = latch_host(s);
-    if (!h) return RCM_ERR_OOM;
-    const int bits = *(volatile int*)h;
-    *(volatile int*)h = 0;
-    return status_from_bits(bits);
+    return status_from_bits(latch_take(s));
 }
 
 rcm_status rcm_bandwidth_profile(int32_t n, const int32_t* rowptr, const int32_t* colidx, const int32_t* perm,

@@ -453,13 +453,25 @@ rcm_status order_single(int32_t n, int64_t nnz, const int32_t* rowptr, const int
     rcm_status st = single_launch(n, nnz, o, &sl);
     if (st != RCM_OK) return st;
     const SingleLayout L = single_layout(n, nnz, true, sl.async && !sl.small, sl.hybrid && !sl.small);
+    int* latch = stream_latch(s);
+    if (!latch) return RCM_ERR_TOO_LARGE;  // every latch slot held by streams whose status is unread
+    // the L2 window raises the context's persisting-L2 limit for the traversal; the call waits for
+    // its work and puts the previous limit back (a raised limit slows the caller's later kernels)
+    const bool window = sl.l2_persist && !sl.small && !sl.cluster;
+    size_t prev_limit = 0;
+    if (window && cudaDeviceGetLimit(&prev_limit, cudaLimitPersistingL2CacheSize) != cudaSuccess) return RCM_ERR_CUDA;
     void* ws = nullptr;
     st = ws_alloc(&ws, L.total, s);
     if (st != RCM_OK) return st;
     char* base = (char*)ws;
     cudaError_t e = enqueue_single(n, nnz, rowptr, colidx, perm, base, L, sl, ev, s);
-    if (e == cudaSuccess) e = enqueue_latch((Ctl*)(base + L.ctl), stream_latch(s), stats_dev, s);
+    if (e == cudaSuccess) e = enqueue_latch((Ctl*)(base + L.ctl), latch, stats_dev, s);
     ws_free(ws, s);
+    if (window) {
+        const cudaError_t e2 = cudaStreamSynchronize(s);
+        const cudaError_t e3 = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, prev_limit);
+        if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : e3;
+    }
     return e == cudaSuccess ? RCM_OK : cuda_status(e);
 }
 

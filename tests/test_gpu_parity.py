@@ -296,6 +296,9 @@ OPTION_SETS = [
     {"expand_mode": 1, "narrow_threshold": -1},                    # top-down only
     {"expand_mode": 3, "narrow_threshold": -1},                    # chosen per level
     {"expand_mode": 3, "bottom_up_divisor": 1000000},              # per level, switching early
+    {"l2_persist": 1, "executor": 1},                              # claims and stamps persisting in L2
+    {"l2_persist": 1, "narrow_threshold": -1, "fused_sweeps": 1},
+    {"fused_sweeps": 2, "executor": 1, "grid_blocks": 8},          # every sweep labelled on a small grid
 ]
 
 
@@ -506,6 +509,68 @@ def test_key_order_field_guard():
     assert np.array_equal(perm.cpu().numpy(), oracle.rcm(g.n, g.rowptr, g.colidx))
     o.debug_order_bits = 63                                           # wider than the level leaves room for
     assert rcm.rcm_order_ex(g.n, rp, ci, perm, o, None) == rcm.RCM_ERR_INVALID_ARG
+
+
+def test_latch_slots_are_freed_and_refused_when_all_are_held():
+    """Every stream an ordering ran on holds one of 4,096 latch words until rcm_stream_status reads
+    it. Ordering on new streams without reading their status ends with RCM_ERR_TOO_LARGE (before
+    any work) once all are held, never with two streams sharing a word; reading one stream's status
+    frees a word for the next stream."""
+    rcm = rcm_mod()
+    g = synth.path(50, seed=3)
+    rp, ci = to_dev(g)
+    want = oracle.rcm(g.n, g.rowptr, g.colidx)
+    o = rcm.rcm_options()
+    o.executor, o.nnz = 2, g.nnz
+    streams, outs, refused = [], [], None
+    try:
+        for _ in range(4097):
+            st = torch.cuda.Stream()
+            out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+            status = rcm.rcm_order_ex(g.n, rp, ci, out, o, None, st)
+            if status == rcm.RCM_ERR_TOO_LARGE:
+                refused = st
+                break
+            assert status == rcm.RCM_OK
+            streams.append(st)
+            outs.append(out)
+        assert refused is not None and len(streams) <= 4096
+        assert rcm.rcm_stream_status(streams[0]) == rcm.RCM_OK          # frees its word
+        out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        assert rcm.rcm_order_ex(g.n, rp, ci, out, o, None, refused) == rcm.RCM_OK
+        assert rcm.rcm_stream_status(refused) == rcm.RCM_OK
+        assert np.array_equal(out.cpu().numpy(), want)
+    finally:
+        for st in streams[1:]:
+            rcm.rcm_stream_status(st)
+    for out in outs[::512]:
+        assert np.array_equal(out.cpu().numpy(), want)
+
+
+def test_l2_window_restores_the_context_limit():
+    """rcm_options.l2_persist raises the context's persisting-L2 limit for the traversal only: the
+    call gives the oracle's order and leaves the limit as it found it (a raised limit slows later
+    kernels of the context)."""
+    import ctypes
+
+    rcm = rcm_mod()
+    cu = ctypes.CDLL("libcuda.so.1")
+
+    def limit():
+        v = ctypes.c_size_t()
+        assert cu.cuCtxGetLimit(ctypes.byref(v), 6) == 0          # CU_LIMIT_PERSISTING_L2_CACHE_SIZE
+        return v.value
+
+    g = synth.grid((60, 60, 60), seed=141)
+    rp, ci = to_dev(g)
+    perm = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    o = rcm.rcm_options()
+    o.executor, o.l2_persist = 1, 1
+    before = limit()
+    rcm.check(rcm.rcm_order_ex(g.n, rp, ci, perm, o, None), "l2 window")
+    assert limit() == before
+    rcm.check(rcm.rcm_stream_status(), "l2 window")
+    assert np.array_equal(perm.cpu().numpy(), oracle.rcm(g.n, g.rowptr, g.colidx))
 
 
 def test_bandwidth_profile_matches_oracle():
