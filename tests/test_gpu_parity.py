@@ -515,24 +515,29 @@ def test_latch_slots_are_freed_and_refused_when_all_are_held():
     """Every stream an ordering ran on holds one of 4,096 latch words until rcm_stream_status reads
     it. Ordering on new streams without reading their status ends with RCM_ERR_TOO_LARGE (before
     any work) once all are held, never with two streams sharing a word; reading one stream's status
-    frees a word for the next stream."""
+    frees a word for the next stream. (Raw driver streams: torch hands out pooled streams.)"""
+    import ctypes
+
     rcm = rcm_mod()
+    cu = ctypes.CDLL("libcuda.so.1")
     g = synth.path(50, seed=3)
     rp, ci = to_dev(g)
     want = oracle.rcm(g.n, g.rowptr, g.colidx)
     o = rcm.rcm_options()
     o.executor, o.nnz = 2, g.nnz
+    torch.cuda.synchronize()
     streams, outs, refused = [], [], None
     try:
         for _ in range(4097):
-            st = torch.cuda.Stream()
+            h = ctypes.c_void_p()
+            assert cu.cuStreamCreate(ctypes.byref(h), 1) == 0          # CU_STREAM_NON_BLOCKING
             out = torch.empty(g.n, dtype=torch.int32, device="cuda")
-            status = rcm.rcm_order_ex(g.n, rp, ci, out, o, None, st)
+            status = rcm.rcm_order_ex(g.n, rp, ci, out, o, None, h.value)
             if status == rcm.RCM_ERR_TOO_LARGE:
-                refused = st
+                refused = h.value
                 break
             assert status == rcm.RCM_OK
-            streams.append(st)
+            streams.append(h.value)
             outs.append(out)
         assert refused is not None and len(streams) <= 4096
         assert rcm.rcm_stream_status(streams[0]) == rcm.RCM_OK          # frees its word
@@ -540,11 +545,15 @@ def test_latch_slots_are_freed_and_refused_when_all_are_held():
         assert rcm.rcm_order_ex(g.n, rp, ci, out, o, None, refused) == rcm.RCM_OK
         assert rcm.rcm_stream_status(refused) == rcm.RCM_OK
         assert np.array_equal(out.cpu().numpy(), want)
+        for st in streams[1:]:
+            assert rcm.rcm_stream_status(st) == rcm.RCM_OK
+        for out in outs[::512]:
+            assert np.array_equal(out.cpu().numpy(), want)
     finally:
         for st in streams[1:]:
             rcm.rcm_stream_status(st)
-    for out in outs[::512]:
-        assert np.array_equal(out.cpu().numpy(), want)
+        for st in streams + ([refused] if refused else []):
+            cu.cuStreamDestroy_v2(ctypes.c_void_p(st))
 
 
 def test_l2_window_restores_the_context_limit():
