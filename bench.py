@@ -59,6 +59,8 @@ def parse_args():
     p.add_argument("--fifo-requests", type=int, default=500,
                    help="requests of the served trace replayed FIFO through rcm_order_host (a prefix)")
     p.add_argument("--no-configs", action="store_true", help="skip the 64x64 grid, mesh and power-law lines")
+    p.add_argument("--cpu-serve-requests", type=int, default=200,
+                   help="requests of the served trace the all-core oracle baseline orders (a prefix)")
     p.add_argument("--launch", default=None,
                    help="options of the one-graph engine, skipping the autotuner: key=value pairs such as "
                         "executor=1,narrow_threshold=512 (or a JSON object)")
@@ -128,14 +130,15 @@ def parse_launch(text: str) -> dict:
     return out
 
 
-def recorded_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from a committed ncu summary, only if the kernel sources still match."""
+def recorded_traffic(kernel: str, workload: str, launch: dict | None = None):
+    """DRAM bytes per launch from a committed ncu summary, only if the kernel sources still match
+    and the capture ran the same launch options (when given)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         e = d[kernel][workload]
-        if e.get("sources") == kernel_sources_hash():
+        if e.get("sources") == kernel_sources_hash() and (launch is None or e.get("launch") == launch):
             return int(e["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -478,6 +481,22 @@ def bench_served(args, torch, rcm, synth, workers):
     out["capacity"] = {"what": "the same requests submitted at once (continuous batching at full load)",
                        "orderings_per_s": cap["orderings_per_s"], "p50_ms": cap["p50_ms"], "p99_ms": cap["p99_ms"],
                        "max_concurrent": cap["max_concurrent"]}
+    if not args.no_cpu_baseline and args.cpu_serve_requests > 0:
+        # the oracle over all host cores, one request per thread, on the trace's first requests
+        from concurrent.futures import ThreadPoolExecutor
+
+        import oracle
+
+        k = min(args.cpu_serve_requests, len(setup["which"]))
+        graphs = [setup["pool"][int(gi)] for gi in setup["which"][:k]]
+        cores = len(os.sched_getaffinity(0))
+        oracle.load()
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(max_workers=cores) as ex:
+            list(ex.map(lambda g: oracle.rcm(g.n, g.rowptr, g.colidx), graphs))
+        t_cpu = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": k / t_cpu, "unit": "orderings/s", "cores": cores, "kind": "oracle",
+                               "sample": f"the trace's first {k} requests, one request per thread"}
     return out
 
 
@@ -635,7 +654,7 @@ def main():
     trav = statistics.mean(trav_ms)
     achieved = alg / (trav / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": recorded_traffic("k_rcm_single", f"grid{args.side}"),
+                "traffic": recorded_traffic("k_rcm_single", f"grid{args.side}", tuned),
                 "kernel": "k_rcm_single", "kernel_ms": trav, "algorithmic_bytes": alg,
                 "peak_kind": f"{peak_kind} hbm_gbs (copy)"}
 
