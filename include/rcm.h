@@ -142,6 +142,14 @@ typedef struct {
                                   always fits on at least one). With a forced width that clamp is
                                   skipped, and a level share that does not fit ends the call with
                                   RCM_ERR_TOO_LARGE. 1..(the width from n), else RCM_ERR_INVALID_ARG */
+    int32_t mid_cluster;       /* middle tier of the persistent grid: the grid is launched in thread-
+                                  block clusters of this many CTAs (2, 4, 8 or 16, as the device
+                                  allows; the grid shrinks to the CTAs that fit in whole clusters),
+                                  and labelled levels of narrow_threshold to mid_cluster x the CTA
+                                  width vertices run on cluster 0 alone, exchanging through
+                                  distributed shared memory instead of the grid's L2 atomics. Same
+                                  result. 0 or -1 = off; cooperative grid only (not with cluster,
+                                  RCM_ERR_INVALID_ARG otherwise)                                    */
 } rcm_options;
 
 /* Statistics of one ordering (filled by rcm_order_ex when requested). */

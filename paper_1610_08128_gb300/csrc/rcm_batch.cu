@@ -104,6 +104,8 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_rcm_
         a.aq = nullptr;
         a.actl = nullptr;
         a.aq_cap = 0;
+        a.mid_k = 0;  // CTA engines: no middle tier
+        a.mid_thr = 0;
         __syncthreads();
         e.init(a, &smem);
         e.sm_sort = s_sort;

@@ -180,6 +180,9 @@ static rcm_status check_options(const rcm_options* o) {
     if (o->expand_mode < 0 || o->expand_mode > 3 || o->bottom_up_divisor < 0) return RCM_ERR_INVALID_ARG;
     if (o->fused_sweeps < -1 || o->fused_sweeps > 2 || o->l2_persist < -1 || o->l2_persist > 1) return RCM_ERR_INVALID_ARG;
     if (o->debug_order_bits < 0 || o->debug_order_bits > 63) return RCM_ERR_INVALID_ARG;
+    if (o->mid_cluster != 0 && o->mid_cluster != -1 && o->mid_cluster != 2 && o->mid_cluster != 4 &&
+        o->mid_cluster != 8 && o->mid_cluster != 16)
+        return RCM_ERR_INVALID_ARG;
     return RCM_OK;
 }
 

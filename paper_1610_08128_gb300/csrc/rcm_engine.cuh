@@ -92,6 +92,11 @@ struct EngineArgs {
     unsigned long long* aq;      // work queue of aq_cap (distance << 32 | vertex) items
     AsyncCtl* actl;
     unsigned aq_cap;
+    // middle tier (whole-grid executor launched in clusters of mid_k CTAs; 0 = off): labelled
+    // levels of narrow_thr <= size < mid_thr run on cluster 0 alone, exchanging through
+    // distributed shared memory, while the other CTAs wait at the next grid barrier
+    int mid_k;
+    int mid_thr;
 };
 
 enum { kPhExpand = 0, kPhClaim, kPhOwn, kPhLabels, kPhExchange, kPhRedist, kPhWaitNarrow, kPhOther };
@@ -111,6 +116,10 @@ struct EngineSmem {
     unsigned long long bck;
     int tail;
     int aflag;                   // async sweep: stop flag relayed to the CTA's warps
+    // middle tier: this CTA's part of each cluster exchange, read by the cluster's CTAs through
+    // distributed shared memory; double-buffered by epoch parity
+    unsigned long long xc_flag[2];  // (epoch << 32) | count, released at cluster scope
+    unsigned long long xc_key[2];   // min (degree, id) key of the CTA's slice
     int cache[2][kCache];
 };
 
@@ -141,6 +150,7 @@ struct Engine {
     static_assert(!kBottomUp || !kCtaOnly, "bottom-up levels need the whole grid");
     const EngineArgs* a;   // in shared memory (keeps the per-thread register footprint small)
     unsigned epoch;
+    unsigned cepoch;       // middle-tier exchanges so far
     int sweep_id;
     int scan_par;          // alternates between consecutive CTA scans (see block_excl_scan)
     bool async_ok;         // asynchronous levels-only sweeps still enabled (off once the queue ran full)
@@ -162,6 +172,7 @@ struct Engine {
         __syncthreads();
         a = &smem->args;
         epoch = 0;
+        cepoch = 0;
         sweep_id = 0;
         scan_par = 0;
         async_ok = true;
@@ -378,6 +389,98 @@ struct Engine {
     __device__ bool barrier() {
         ExResult r;
         return exchange(r, false);
+    }
+
+    // ---- the middle tier's exchange: the mid_k CTAs of cluster 0 ----
+    // Each CTA publishes (epoch << 32) | count in its own shared memory with a cluster-scope release
+    // (after a CTA barrier, so its claims are released with it); warp 0's lanes poll the peers' words
+    // with cluster-scope acquire loads through distributed shared memory. The words are double-
+    // buffered by epoch parity: a CTA rewrites a slot two epochs later, only after every peer has
+    // published the epoch in between, i.e. finished reading this one. Every wait is bounded by
+    // limit_ns. r receives the total, this CTA's prefix and the largest count (not the key: see
+    // mid_min_key). Returns false if a wait ran out or another CTA failed.
+    __device__ bool exchange_mid(ExResult& r) {
+        __syncthreads();
+        const unsigned e = ++cepoch;
+        const int K = a->mid_k;
+        const int me = (int)cluster_rank();
+        if (threadIdx.x == 0) {
+            sm->xc_key[e & 1] = cta_key();
+            const unsigned cnt = (unsigned)sm->acc_cnt;
+            sm->acc_cnt = 0;
+            st_release_cluster_u64(&sm->xc_flag[e & 1], ((unsigned long long)e << 32) | cnt);
+        }
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            int bad = 0, x = 0, y = 0, mx = 0;
+            if (lane < K) {
+                const unsigned fr = dsmem_addr(&sm->xc_flag[e & 1], (unsigned)lane);
+                unsigned long long f = ld_acquire_cluster_u64(fr);
+                if ((unsigned)(f >> 32) != e) {
+                    const unsigned long long t0 = globaltimer_ns();
+                    unsigned spins = 0;
+                    while ((unsigned)((f = ld_acquire_cluster_u64(fr)) >> 32) != e) {
+                        if ((++spins & 31u) == 0) {
+                            if (ld_volatile(a->status) & (kErrTimeout | kErrInternal | kErrTooLarge)) {
+                                bad = 1;
+                                break;
+                            }
+                            if ((long long)(globaltimer_ns() - t0) > a->limit_ns) {
+                                atomicOr(a->status, kErrTimeout);
+                                bad = 1;
+                                break;
+                            }
+                        }
+                    }
+                }
+                if (!bad) {
+                    const int v = (int)(unsigned)(f & 0xffffffffu);
+                    y = v;
+                    x = lane < me ? v : 0;
+                    mx = v;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                x += __shfl_xor_sync(0xffffffffu, x, o);
+                y += __shfl_xor_sync(0xffffffffu, y, o);
+                mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+            }
+            if (lane == 0) {
+                // a member that failed set the status before publishing: every member sees it here
+                if (ld_volatile(a->status) & (kErrTimeout | kErrInternal | kErrTooLarge)) bad = 1;
+                sm->ex[0] = y;
+                sm->ex[1] = x;
+                sm->ex[2] = mx;
+                sm->ex[3] = bad;
+            }
+        }
+        __syncthreads();
+        r.total = sm->ex[0];
+        r.pre = sm->ex[1];
+        r.maxcnt = sm->ex[2];
+        r.key = kKeyMax;
+        const bool ok = sm->ex[3] == 0;
+        __syncthreads();
+        return ok;
+    }
+
+    // Min over the cluster-0 CTAs of the keys published at middle-tier exchange e. Valid after
+    // exchange e + 1 as long as no CTA has started exchange e + 2 (true where it is used: the
+    // run's end, before the grid barrier every CTA must reach).
+    __device__ unsigned long long mid_min_key(unsigned e) {
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            unsigned long long k = kKeyMax;
+            if (lane < a->mid_k) k = ld_dsmem_u64(dsmem_addr(&sm->xc_key[e & 1], (unsigned)lane));
+            k = warp_min_u64(k);
+            if (lane == 0) sm->ex_key = k;
+        }
+        __syncthreads();
+        const unsigned long long k = sm->ex_key;
+        __syncthreads();
+        return k;
     }
 
     // ---------------- levels-only level ----------------
@@ -1183,6 +1286,25 @@ struct Engine {
         }
     }
 
+    // The slices of a level numbered at labels [lstart, lstart + F), for the tier that runs it
+    // next: CTA 0 alone below narrow_thr; the CTAs of cluster 0 below mid_thr (middle tier on);
+    // otherwise the whole grid, in balanced slices.
+    __device__ void choose_tier(int F, int lstart, bool& narrow, bool& mid, Slice& cur) const {
+        const int b = cta_rank(), B = cta_count();
+        narrow = F < a->narrow_thr;
+        mid = !narrow && a->mid_k > 0 && F < a->mid_thr;
+        if (narrow) {
+            cur = perm_range(lstart, b == 0 ? F : 0);
+        } else if (mid) {
+            const int K = a->mid_k;
+            const int lo = b < K ? (int)((long long)F * b / K) : 0, hi = b < K ? (int)((long long)F * (b + 1) / K) : 0;
+            cur = perm_range(lstart + lo, hi - lo);
+        } else {
+            const int lo = (int)((long long)F * b / B), hi = (int)((long long)F * (b + 1) / B);
+            cur = perm_range(lstart + lo, hi - lo);
+        }
+    }
+
     // Labelled sweep from root, labels from nv. On return: ecc, the min (degree, id) key of the
     // last level, and the component size (labels nv .. nv+size-1).
     __device__ bool sweep_labelled(int root, int nv, int& ecc, unsigned long long& last_key, int& size) {
@@ -1205,6 +1327,7 @@ struct Engine {
         cur.step = 1;
         cur.cnt = (b == 0) ? 1 : 0;
         bool narrow = kCtaOnly || a->narrow_thr > 1;
+        bool mid = false;   // the middle tier runs the current level
         int F = 1;          // level size (known in narrow runs and after redistribution)
         // the last completed level (grid runs detect the end one level late)
         int prev_start = nv, prev_size = 1;
@@ -1283,11 +1406,109 @@ struct Engine {
                     size = lstart + lastF2 - nv;
                     return true;
                 }
-                // whole grid from here: balanced slices of the level's label range in perm
-                const int lo = (int)((long long)F * b / B), hi = (int)((long long)F * (b + 1) / B);
-                cur = perm_range(lstart + lo, hi - lo);
-                narrow = false;
+                // the middle tier or the whole grid from here: slices of the level's label range in perm
+                choose_tier(F, lstart, narrow, mid, cur);
                 continue;
+            }
+            if constexpr (!kCtaOnly) {
+                if (mid) {
+                    // ---- middle tier: levels run by the CTAs of cluster 0, ord = b * mslot + j ----
+                    // Same phases as a whole-grid level; the exchange goes through distributed
+                    // shared memory. The run ends when a level leaves [narrow_thr, mid_thr) or gets
+                    // out of balance: the next level is counted and numbered, published, and every
+                    // CTA takes its slice of it from perm after the grid barrier.
+                    const int K = a->mid_k;
+                    if (b < K) {
+                        const unsigned long long mslot = ((1ull << a->obits) - 1ull) / (unsigned long long)K;
+                        int F2 = 0, fin_start = 0, fin_size = 0, fin_ecc = 0;
+                        unsigned long long fin_key = kKeyMax;
+                        while (true) {
+                            if ((unsigned long long)cur.cnt > mslot) fail(kErrTooLarge);  // every member's exchange fails
+                            const unsigned long long ord0 = (unsigned long long)b * mslot;
+                            int u0;
+                            int r0[8];
+                            phase_a(d, ord0, cur, u0, r0);
+                            if (threadIdx.x == 0) atomicAdd(&sm->acc_cnt, cur.cnt);
+                            tick(kPhClaim);
+                            ExResult r;
+                            if (!exchange_mid(r)) return false;
+                            tick(kPhExchange);
+                            stat_add(kStGrid, 1);
+                            if (r.total == 0) {  // level d is empty: the sweep ended with level d - 1
+                                fin_key = mid_min_key(cepoch - 1);
+                                fin_ecc = d - 1;
+                                fin_start = prev_start;
+                                fin_size = prev_size;
+                                break;
+                            }
+                            write_labels(cur, lstart + r.pre);
+                            tick(kPhLabels);
+                            if (b == 0 && threadIdx.x == 0) c->qtail[(d + 2) % 3] = 0;
+                            Slice nxt;
+                            int* stage = (d & 1) ? a->qa : a->qb;
+                            const int kids = phase_b(d, ord0, cur, u0, r0, sm->cache[cb ^ 1], stage,
+                                                     &c->qtail[(d + 1) % 3], -1, lstart + r.pre - nv, &nxt);
+                            tick(kPhOwn);
+                            prev_start = lstart;
+                            prev_size = r.total;
+                            lstart += r.total;
+                            if (++d > a->n) {
+                                fail_at(kSiteLevels, d);
+                                return false;
+                            }
+                            cur = nxt;
+                            if (cur.sh) cb ^= 1;
+                            const int fair = (r.total + K - 1) / K;
+                            if (r.total < a->narrow_thr || r.total >= a->mid_thr || r.maxcnt > 2 * fair + 64) {
+                                if (threadIdx.x == 0) atomicAdd(&sm->acc_cnt, kids);
+                                ExResult r2;
+                                if (!exchange_mid(r2)) return false;
+                                if (r2.total == 0) {
+                                    fin_key = mid_min_key(cepoch - 1);
+                                    fin_ecc = d - 1;
+                                    fin_start = prev_start;
+                                    fin_size = prev_size;
+                                    break;
+                                }
+                                write_labels(cur, lstart + r2.pre);
+                                F2 = r2.total;
+                                break;
+                            }
+                        }
+                        if (b == 0 && threadIdx.x == 0) {
+                            c->pub_F = F2;
+                            c->pub_start = F2 > 0 ? lstart : fin_start;
+                            c->pub_ecc = F2 > 0 ? d : fin_ecc;
+                            c->pub_lastF = fin_size;
+                            c->pub_key = fin_key;
+                        }
+                    }
+                    tick(kPhOther);
+                    if (!barrier()) return false;
+                    tick(kPhWaitNarrow);
+                    if (threadIdx.x == 0) {
+                        sm->bc[0] = ldcg(&c->pub_F);
+                        sm->bc[1] = ldcg(&c->pub_start);
+                        sm->bc[2] = ldcg(&c->pub_ecc);
+                        sm->bc[3] = ldcg(&c->pub_lastF);
+                        sm->bck = __ldcg(&c->pub_key);
+                    }
+                    __syncthreads();
+                    F = sm->bc[0];
+                    lstart = sm->bc[1];
+                    d = sm->bc[2];
+                    const int lastF3 = sm->bc[3];
+                    const unsigned long long lk3 = sm->bck;
+                    __syncthreads();
+                    if (F == 0) {
+                        last_key = lk3;
+                        ecc = d;
+                        size = lstart + lastF3 - nv;
+                        return true;
+                    }
+                    choose_tier(F, lstart, narrow, mid, cur);
+                    continue;
+                }
             }
             // ---- whole-grid level d: this CTA's slice, ord = b * slot + j ----
             if ((unsigned long long)cur.cnt > slot) {
@@ -1340,8 +1561,8 @@ struct Engine {
             cur = nxt;
             if (cur.sh) cb ^= 1;
             const int fair = (r.total + B - 1) / B;
-            if (r.total < a->narrow_thr || r.maxcnt > 2 * fair + 64) {
-                // number level d now and redistribute it (or hand it to CTA 0)
+            if (r.total < a->narrow_thr || (a->mid_k > 0 && r.total < a->mid_thr) || r.maxcnt > 2 * fair + 64) {
+                // number level d now and redistribute it (or hand it to CTA 0 or the middle tier)
                 if (threadIdx.x == 0) atomicAdd(&sm->acc_cnt, kids);
                 ExResult r2;
                 if (!exchange(r2)) return false;
@@ -1355,13 +1576,7 @@ struct Engine {
                 if (!barrier()) return false;
                 tick(kPhRedist);
                 F = r2.total;
-                if (F < a->narrow_thr) {
-                    narrow = true;
-                    cur = perm_range(lstart, b == 0 ? F : 0);
-                    continue;
-                }
-                const int lo = (int)((long long)F * b / B), hi = (int)((long long)F * (b + 1) / B);
-                cur = perm_range(lstart + lo, hi - lo);
+                choose_tier(F, lstart, narrow, mid, cur);
             }
         }
     }

@@ -107,6 +107,47 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// ---- distributed shared memory of a thread-block cluster ----
+
+// This CTA's rank inside its cluster (0 for launches without clusters).
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Hardware barrier of every thread of the cluster (all threads of all its CTAs must arrive).
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Address of the same shared variable in the CTA of cluster rank `rank`.
+__device__ __forceinline__ unsigned dsmem_addr(const void* local, unsigned rank) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((unsigned)__cvta_generic_to_shared(local)), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_cluster_u64(unsigned dsmem) {
+    unsigned long long v;
+    asm volatile("ld.acquire.cluster.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(dsmem) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_dsmem_u64(unsigned dsmem) {
+    unsigned long long v;
+    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(dsmem) : "memory");
+    return v;
+}
+
+// Release store to this CTA's own shared memory, at cluster scope: what this thread (and, through
+// a preceding CTA barrier, its CTA) wrote before becomes visible to the cluster's threads that
+// acquire the word.
+__device__ __forceinline__ void st_release_cluster_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.cluster.shared::cta.u64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "l"(v)
+                 : "memory");
+}
+
 // Coherent (L2) load for data written by other CTAs during this kernel.
 __device__ __forceinline__ int ldcg(const int* p) { return __ldcg(p); }
 

@@ -151,6 +151,38 @@ int single_cluster_max() {
     return g_cluster_max;
 }
 
+// CTAs of the persistent grid (threads wide) that fit the device co-resident in whole clusters of
+// k CTAs, launched cooperatively: 0 if the device cannot launch such clusters. Cached per shape.
+static int g_mid_fit[8][5];
+static int mid_cluster_fit(int threads, bool async, bool hybrid, int k) {
+    const int kidx = k == 2 ? 0 : k == 4 ? 1 : k == 8 ? 2 : k == 16 ? 3 : -1;
+    const int tidx = async ? 6 : hybrid ? 7 : threads_index(threads);
+    if (kidx < 0 || tidx < 0) return 0;
+    std::lock_guard<std::mutex> g(g_single_mu);
+    if (g_mid_fit[tidx][kidx] == 0) {
+        const void* kern = single_kernel(threads, async, hybrid);
+        if (k > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(k);
+        cfg.blockDim = dim3(threads);
+        cfg.dynamicSmemBytes = kSingleDynSmem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = k;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            clusters = 0;
+        }
+        g_mid_fit[tidx][kidx] = clusters > 0 ? clusters * k : -1;
+    }
+    return std::max(g_mid_fit[tidx][kidx], 0);
+}
+
 static std::once_flag g_small_once;
 static cudaError_t g_small_attr = cudaSuccess;
 
@@ -210,6 +242,7 @@ rcm_status single_launch(int n, long long nnz, const rcm_options& o, SingleLaunc
     const int per_sm = single_blocks_per_sm(sl.threads, sl.async, sl.hybrid);
     if (per_sm <= 0) return RCM_ERR_CUDA;
     sl.cluster = o.cluster != 0;
+    if (o.mid_cluster > 0 && sl.cluster) return RCM_ERR_INVALID_ARG;
     if (sl.cluster) {
         // one cluster: only the 512-thread engine is set up for it
         const int cmax = sl.threads == 512 ? single_cluster_max() : 0;
@@ -219,6 +252,14 @@ rcm_status single_launch(int n, long long nnz, const rcm_options& o, SingleLaunc
         const int max_blocks = std::min(per_sm * di.sms, kMaxGridBlocks);
         sl.blocks = o.grid_blocks ? o.grid_blocks : di.sms;
         if (sl.blocks < 1 || sl.blocks > max_blocks) return RCM_ERR_INVALID_ARG;
+        if (o.mid_cluster > 0) {
+            // the middle tier: whole clusters only, as many as fit co-resident
+            const int k = o.mid_cluster;
+            const int fit = mid_cluster_fit(sl.threads, sl.async, sl.hybrid, k);
+            sl.blocks = std::min(sl.blocks, fit) / k * k;
+            if (sl.blocks < k) return RCM_ERR_INVALID_ARG;
+            sl.mid_k = k;
+        }
     }
     // claim keys: (level + 1) in the high bits, the in-level order b * slot + j in the low obits;
     // slot = (2^obits - 1) / blocks must exceed any slice size (< n). A forced width (test hook)
@@ -230,6 +271,10 @@ rcm_status single_launch(int n, long long nnz, const rcm_options& o, SingleLaunc
     if ((unsigned long long)sl.blocks > slot_cap && o.debug_order_bits == 0) {
         if (sl.cluster) return RCM_ERR_TOO_LARGE;
         sl.blocks = (int)std::max(1ull, slot_cap);
+        if (sl.mid_k > 0) {  // whole clusters, or no middle tier
+            sl.blocks = sl.blocks >= sl.mid_k ? sl.blocks / sl.mid_k * sl.mid_k : sl.blocks;
+            if (sl.blocks < sl.mid_k) sl.mid_k = 0;
+        }
     }
     // narrow runs keep the frontier in a shared-memory cache of kCache ids
     // default switch at the CTA width: for 512-thread CTAs it beat twice the width on every graph
@@ -259,35 +304,51 @@ rcm_status single_launch(int n, long long nnz, const rcm_options& o, SingleLaunc
 // arrays, which every level's atomics hit at random -- marked persisting in L2, so that the rows
 // streaming through L2 do not evict them. The context's persisting-L2 limit is raised to the
 // window (clamped to the device maximum) on first use.
-static cudaError_t launch_persisting(const void* kernel, const SingleLaunch& sl, void** kargs, char* win, size_t bytes,
-                                     cudaStream_t s) {
-    int dev = 0, max_persist = 0, max_window = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev);
-    if (e != cudaSuccess) return e;
-    const size_t window = std::min(bytes, (size_t)max_window);
-    const size_t persist = std::min(window, (size_t)max_persist);
-    size_t cur = 0;
-    e = cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
-    if (e == cudaSuccess && cur < persist) e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, persist);
-    if (e != cudaSuccess) return e;
+static cudaError_t launch_grid(const void* kernel, const SingleLaunch& sl, void** kargs, char* win, size_t bytes,
+                               cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(sl.blocks);
     cfg.blockDim = dim3(sl.threads);
     cfg.dynamicSmemBytes = kSingleDynSmem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[2];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    attr[1].id = cudaLaunchAttributeAccessPolicyWindow;
-    attr[1].val.accessPolicyWindow.base_ptr = win;
-    attr[1].val.accessPolicyWindow.num_bytes = window;
-    attr[1].val.accessPolicyWindow.hitRatio = window ? std::min(1.0f, (float)persist / (float)window) : 0.0f;
-    attr[1].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
-    attr[1].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    cudaLaunchAttribute attr[3];
+    int na = 0;
+    attr[na].id = cudaLaunchAttributeCooperative;
+    attr[na].val.cooperative = 1;
+    ++na;
+    if (sl.mid_k > 0) {
+        attr[na].id = cudaLaunchAttributeClusterDimension;
+        attr[na].val.clusterDim.x = sl.mid_k;
+        attr[na].val.clusterDim.y = 1;
+        attr[na].val.clusterDim.z = 1;
+        ++na;
+    }
+    if (sl.l2_persist) {
+        // [win, win + bytes) -- the claim and stamp arrays, which every level's atomics hit at
+        // random -- marked persisting in L2, so that the rows streaming through L2 do not evict
+        // them; the context's persisting-L2 limit is raised to the window (clamped to the device
+        // maximum), and order_single puts it back after the call
+        int dev = 0, max_persist = 0, max_window = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev);
+        if (e != cudaSuccess) return e;
+        const size_t window = std::min(bytes, (size_t)max_window);
+        const size_t persist = std::min(window, (size_t)max_persist);
+        size_t cur = 0;
+        e = cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+        if (e == cudaSuccess && cur < persist) e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, persist);
+        if (e != cudaSuccess) return e;
+        attr[na].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[na].val.accessPolicyWindow.base_ptr = win;
+        attr[na].val.accessPolicyWindow.num_bytes = window;
+        attr[na].val.accessPolicyWindow.hitRatio = window ? std::min(1.0f, (float)persist / (float)window) : 0.0f;
+        attr[na].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        attr[na].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        ++na;
+    }
     cfg.attrs = attr;
-    cfg.numAttrs = 2;
+    cfg.numAttrs = na;
     return cudaLaunchKernelExC(&cfg, kernel, kargs);
 }
 
@@ -410,6 +471,8 @@ cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* c
     long long slots = std::min<long long>(2LL * n, 1LL << 31);
     if (sl.async_slots > 0) slots = std::min<long long>(slots, sl.async_slots);
     args.aq_cap = async ? (unsigned)slots : 0u;
+    args.mid_k = sl.small ? 0 : sl.mid_k;
+    args.mid_thr = args.mid_k * sl.threads;  // one round of every member CTA
     int stall = sl.stall;
     void* kargs[] = {&args, &stall};
     if (sl.small) {
@@ -430,11 +493,10 @@ cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* c
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         e = cudaLaunchKernelExC(&cfg, single_kernel(sl.threads, async, hybrid), kargs);
-    } else if (sl.l2_persist) {
-        e = launch_persisting(single_kernel(sl.threads, async, hybrid), sl, kargs, base + L.claim,
-                              L.bigrows - L.claim, s);
+    } else if (sl.l2_persist || sl.mid_k > 0) {
+        e = launch_grid(single_kernel(sl.threads, async, hybrid), sl, kargs, base + L.claim, L.bigrows - L.claim, s);
         if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
-        if (e == cudaSuccess) e = release_persisting(base + L.claim, L.bigrows - L.claim, s);
+        if (e == cudaSuccess && sl.l2_persist) e = release_persisting(base + L.claim, L.bigrows - L.claim, s);
         return e;
     } else {
         e = cudaLaunchCooperativeKernel(single_kernel(sl.threads, async, hybrid), dim3(sl.blocks), dim3(sl.threads), kargs,

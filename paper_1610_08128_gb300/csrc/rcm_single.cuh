@@ -45,6 +45,7 @@ struct SingleLaunch {
     int bu_divisor = 16;         // bottom-up once the frontier holds n / bu_divisor vertices
     bool l2_persist = false;     // claims and stamps marked persisting in L2 for the engine's launch
     int obits = 0;               // width of the claim keys' in-level order field (0 = from n)
+    int mid_k = 0;               // middle tier: the grid is launched in clusters of mid_k CTAs (0 = off)
 };
 
 // Derives the launch shape from options for a graph of n vertices and nnz stored entries;

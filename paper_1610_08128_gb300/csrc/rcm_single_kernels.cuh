@@ -45,10 +45,8 @@ extern template __global__ void k_rcm_small<256>(EngineArgs, int, int);
 extern template __global__ void k_rcm_small<512>(EngineArgs, int, int);
 #else
 template <int kThreads, bool kAsync, bool kBottomUp>
-__global__ void __launch_bounds__(kThreads, 1) k_rcm_single(EngineArgs args, int stall) {
-    __shared__ EngineSmem smem;
-    __shared__ int s_item;
-    extern __shared__ unsigned long long s_sort[];  // component-table sort (kCompSmem entries)
+__device__ __forceinline__ void single_run(const EngineArgs& args, int stall, EngineSmem& smem, int& s_item,
+                                           unsigned long long* s_sort) {
     Ctl* ctl = args.ctl;
     if (ld_volatile(&ctl->status) & kErrBadCsr) return;
     if (stall && blockIdx.x == 0) return;  // test hook: the other CTAs' first wait runs out
@@ -157,6 +155,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_rcm_single(EngineArgs args, int
             else if (i != kStIsolated && i != kStGrid) atomicAdd((unsigned long long*)&ctl->stats[i], (unsigned long long)smem.st[i]);
         }
     }
+}
+
+template <int kThreads, bool kAsync, bool kBottomUp>
+__global__ void __launch_bounds__(kThreads, 1) k_rcm_single(EngineArgs args, int stall) {
+    __shared__ EngineSmem smem;
+    __shared__ int s_item;
+    extern __shared__ unsigned long long s_sort[];  // component-table sort (kCompSmem entries)
+    // launched in clusters for the middle tier: every CTA's exchange words are cleared before any
+    // peer can read them, and no CTA leaves while a peer may still read its shared memory (every
+    // path of single_run ends: all its waits are bounded)
+    if (args.mid_k > 0) {
+        if (threadIdx.x == 0) smem.xc_flag[0] = smem.xc_flag[1] = 0ull;
+        cluster_barrier();
+    }
+    single_run<kThreads, kAsync, kBottomUp>(args, stall, smem, s_item, s_sort);
+    if (args.mid_k > 0) cluster_barrier();
 }
 
 

@@ -47,6 +47,7 @@ class rcm_options(ctypes.Structure):
         ("bottom_up_divisor", ctypes.c_int32),
         ("l2_persist", ctypes.c_int32),
         ("debug_order_bits", ctypes.c_int32),
+        ("mid_cluster", ctypes.c_int32),
     ]
 
 

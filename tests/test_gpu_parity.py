@@ -299,6 +299,12 @@ OPTION_SETS = [
     {"l2_persist": 1, "executor": 1},                              # claims and stamps persisting in L2
     {"l2_persist": 1, "narrow_threshold": -1, "fused_sweeps": 1},
     {"fused_sweeps": 2, "executor": 1, "grid_blocks": 8},          # every sweep labelled on a small grid
+    {"mid_cluster": 4, "executor": 1},                             # middle tier on a cluster of 4
+    {"mid_cluster": 8, "executor": 1, "narrow_threshold": 32},     # ... of 8, entered early
+    {"mid_cluster": 2, "executor": 1, "narrow_threshold": -1},     # no CTA-0 levels: grid and middle tier only
+    {"mid_cluster": 8, "executor": 1, "l2_persist": 1},
+    {"mid_cluster": 4, "expand_mode": 3, "bottom_up_divisor": 1000000},  # with bottom-up grid levels
+    {"mid_cluster": 16, "executor": 1, "fused_sweeps": 1},
 ]
 
 
@@ -668,6 +674,19 @@ def test_c2_grid192_full_size():
             continue  # the shared-memory CTA takes at most 4,608 vertices
         assert np.array_equal(gpu_perm(g, opts), want), opts
     assert np.array_equal(gpu_perm(g, {"row_order": 1}), oracle.rcm(g.n, g.rowptr, g.colidx, row_order=1))
+
+
+@pytest.mark.slow
+def test_middle_tier_on_high_diameter_grids():
+    """The middle tier (levels of 512 to a few thousand vertices on one cluster) on grids whose
+    levels mostly fall in that range: a 1000x1000 2D grid, a 3D grid, and a 2D grid with rows
+    stored in shuffled order; every cluster size gives the oracle's order."""
+    graphs = [synth.grid((1000, 1000), seed=151), synth.grid((96, 96, 96), seed=152),
+              synth.shuffle_rows(synth.grid((700, 400), seed=153), 154)]
+    for g in graphs:
+        want = oracle.rcm(g.n, g.rowptr, g.colidx)
+        for k in (2, 4, 8, 16):
+            assert np.array_equal(gpu_perm(g, {"executor": 1, "mid_cluster": k}), want), k
 
 
 @pytest.mark.slow
