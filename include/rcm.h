@@ -145,11 +145,13 @@ typedef struct {
     int32_t mid_cluster;       /* middle tier of the persistent grid: the grid is launched in thread-
                                   block clusters of this many CTAs (2, 4, 8 or 16, as the device
                                   allows; the grid shrinks to the CTAs that fit in whole clusters),
-                                  and labelled levels of narrow_threshold to mid_cluster x the CTA
-                                  width vertices run on cluster 0 alone, exchanging through
-                                  distributed shared memory instead of the grid's L2 atomics. Same
-                                  result. 0 or -1 = off; cooperative grid only (not with cluster,
-                                  RCM_ERR_INVALID_ARG otherwise)                                    */
+                                  and labelled levels of narrow_threshold to mid_threshold vertices
+                                  run on cluster 0 alone, exchanging through distributed shared
+                                  memory instead of the grid's L2 atomics. Same result. 0 or -1 =
+                                  off; cooperative grid only (not with cluster, RCM_ERR_INVALID_ARG
+                                  otherwise)                                                        */
+    int32_t mid_threshold;     /* with mid_cluster: levels below this many vertices (and at least
+                                  narrow_threshold) run on the middle tier; 0 = 128 x mid_cluster   */
 } rcm_options;
 
 /* Statistics of one ordering (filled by rcm_order_ex when requested). */

@@ -183,6 +183,7 @@ static rcm_status check_options(const rcm_options* o) {
     if (o->mid_cluster != 0 && o->mid_cluster != -1 && o->mid_cluster != 2 && o->mid_cluster != 4 &&
         o->mid_cluster != 8 && o->mid_cluster != 16)
         return RCM_ERR_INVALID_ARG;
+    if (o->mid_threshold < 0) return RCM_ERR_INVALID_ARG;
     return RCM_OK;
 }
 

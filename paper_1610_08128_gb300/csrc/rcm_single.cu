@@ -259,6 +259,9 @@ rcm_status single_launch(int n, long long nnz, const rcm_options& o, SingleLaunc
             sl.blocks = std::min(sl.blocks, fit) / k * k;
             if (sl.blocks < k) return RCM_ERR_INVALID_ARG;
             sl.mid_k = k;
+            // each member CTA takes a level share it handles in a fraction of a round: the tier is
+            // bounded by its members' throughput (about 15 ns per vertex and CTA), not by its width
+            sl.mid_thr = o.mid_threshold > 0 ? o.mid_threshold : 128 * k;
         }
     }
     // claim keys: (level + 1) in the high bits, the in-level order b * slot + j in the low obits;
@@ -472,7 +475,7 @@ cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* c
     if (sl.async_slots > 0) slots = std::min<long long>(slots, sl.async_slots);
     args.aq_cap = async ? (unsigned)slots : 0u;
     args.mid_k = sl.small ? 0 : sl.mid_k;
-    args.mid_thr = args.mid_k * sl.threads;  // one round of every member CTA
+    args.mid_thr = args.mid_k ? sl.mid_thr : 0;
     int stall = sl.stall;
     void* kargs[] = {&args, &stall};
     if (sl.small) {

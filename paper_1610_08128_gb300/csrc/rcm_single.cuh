@@ -46,6 +46,7 @@ struct SingleLaunch {
     bool l2_persist = false;     // claims and stamps marked persisting in L2 for the engine's launch
     int obits = 0;               // width of the claim keys' in-level order field (0 = from n)
     int mid_k = 0;               // middle tier: the grid is launched in clusters of mid_k CTAs (0 = off)
+    int mid_thr = 0;             // middle tier: levels below this size (and not narrow) run on cluster 0
 };
 
 // Derives the launch shape from options for a graph of n vertices and nnz stored entries;

@@ -48,6 +48,7 @@ class rcm_options(ctypes.Structure):
         ("l2_persist", ctypes.c_int32),
         ("debug_order_bits", ctypes.c_int32),
         ("mid_cluster", ctypes.c_int32),
+        ("mid_threshold", ctypes.c_int32),
     ]
 
 

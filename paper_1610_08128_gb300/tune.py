@@ -26,8 +26,7 @@ SINGLE_CANDIDATES = [
 ] + [
     {"executor": 1, "expand_mode": 1, "narrow_threshold": t, "l2_persist": l2} for t in (512, 1024) for l2 in (-1, 1)
 ] + [
-    {"executor": 1, "expand_mode": 1, "narrow_threshold": 512, "l2_persist": l2, "mid_cluster": k}
-    for k in (4, 8) for l2 in (-1, 1)
+    {"executor": 1, "expand_mode": 1, "narrow_threshold": 512, "l2_persist": 1, "mid_cluster": k} for k in (8, 16)
 ] + [
     {"executor": 1, "expand_mode": 3, "bottom_up_divisor": dv, "narrow_threshold": t}
     for dv in (4, 16, 64) for t in (512, 1024)

@@ -117,7 +117,9 @@ def test_option_checks_come_before_any_device_work(lib):
 
     bad = [("expand_mode", 4), ("expand_mode", -1), ("row_order", 2), ("async_sweeps", 2), ("async_sweeps", -2),
            ("bottom_up_divisor", -1), ("debug_async_slots", -1), ("executor", 3), ("cluster", 2),
-           ("block_threads", 100), ("narrow_threshold", -2), ("grid_blocks", -1), ("spin_limit_ns", -1)]
+           ("block_threads", 100), ("narrow_threshold", -2), ("grid_blocks", -1), ("spin_limit_ns", -1),
+           ("fused_sweeps", 3), ("fused_sweeps", -2), ("l2_persist", 2), ("debug_order_bits", 64),
+           ("debug_order_bits", -1), ("mid_cluster", 3), ("mid_cluster", 32), ("mid_threshold", -1)]
     for field, value in bad:
         o = rcm.rcm_options()
         setattr(o, field, value)

@@ -305,6 +305,9 @@ OPTION_SETS = [
     {"mid_cluster": 8, "executor": 1, "l2_persist": 1},
     {"mid_cluster": 4, "expand_mode": 3, "bottom_up_divisor": 1000000},  # with bottom-up grid levels
     {"mid_cluster": 16, "executor": 1, "fused_sweeps": 1},
+    {"mid_cluster": 8, "executor": 1, "mid_threshold": 8192},      # a tier far wider than the cluster
+    {"mid_cluster": 4, "executor": 1, "mid_threshold": 600},       # a tier of one CTA-0 threshold's width
+    {"mid_cluster": 4, "executor": 1, "mid_threshold": 100},       # bound below the CTA-0 threshold: tier unused
 ]
 
 
