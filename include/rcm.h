@@ -157,7 +157,9 @@ typedef struct {
 /* Statistics of one ordering (filled by rcm_order_ex when requested). */
 typedef struct {
     int64_t components;      /* connected components                                               */
-    int64_t sweeps;          /* level structures computed by the pseudo-peripheral search (Alg. 2) */
+    int64_t sweeps;          /* level structures computed by the pseudo-peripheral search (Alg. 2);
+                                isolated vertices are numbered directly and count none (Alg. 2 on
+                                one vertex would be two one-level sweeps)                        */
     int64_t traversals;      /* breadth-first traversals executed (a fused labelled sweep counts once) */
     int64_t levels;          /* levels expanded over all traversals                                */
     int64_t max_ecc;         /* largest eccentricity of a root                                     */

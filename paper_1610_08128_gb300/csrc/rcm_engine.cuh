@@ -50,6 +50,7 @@ namespace rcm {
 
 constexpr int kEllNb = 7;       // neighbours stored in a vertex's 32-byte row; slot 7 = degree
 constexpr int kCache = 2048;    // frontier ids cached in shared memory per buffer
+constexpr int kTinyMax = 32;    // components of at most this many vertices are ordered by one thread
 constexpr unsigned long long kClaimNone = ~0ull;
 
 struct EngineArgs {
@@ -1646,7 +1647,8 @@ struct Engine {
     // One connected component: sweeps from its start vertex r (Alg. 2), labelled traversal
     // (Alg. 3) with labels from nv. On return, size = the component's vertex count. With
     // all_left >= 0 (the number of vertices not yet numbered), the call stops after the first
-    // sweep when the component is smaller than that, returning size = -1 (nothing numbered).
+    // sweep when the component is smaller than that and small enough for the component table to
+    // order it at least as fast, returning size = -1 (nothing numbered).
     __device__ bool component(int r, int nv, int& size, long long all_left = -1) {
         if (!in_graph(r) || nv < 0 || nv >= a->n) {
             fail_at(kSiteStart, r);
@@ -1668,7 +1670,12 @@ struct Engine {
         } else if (!sweep_levels(r, ecc_prev, k1, reached)) {
             return false;
         }
-        if (all_left >= 0 && reached < all_left) {
+        // The start vertex's component does not hold every vertex left: the others get a component
+        // table. A component the table would order no faster (the grid's share for the whole grid;
+        // a CTA's beyond the one-thread limit) is finished here, its sweep kept: it takes the first
+        // labels either way. A smaller one is left to the table, its sweep discarded.
+        const long long keep_min = !kCtaOnly ? (long long)a->cc_big : (kSmem ? 0 : (long long)kTinyMax + 1);
+        if (all_left >= 0 && reached < all_left && reached < keep_min) {
             size = -1;
             return true;
         }
@@ -1719,6 +1726,111 @@ struct Engine {
             fail(kErrInternal);
             return false;
         }
+        return true;
+    }
+
+    // ---------------- tiny components: one thread each ----------------
+    // A component of a few dozen vertices gives a level-synchronous traversal nothing to share
+    // out: each level is a few vertices between CTA barriers. One thread runs the serial method on
+    // it instead, so a CTA orders up to blockDim tiny components at once. Rows are stored in
+    // (degree, id) order, so a FIFO traversal that appends each dequeued vertex's unvisited
+    // neighbours in row order numbers the component as Alg. 1 does (parents in label order,
+    // children by increasing degree, ties by id); the level boundaries give Alg. 2 its eccentricity
+    // and the last level's minimum (degree, id) vertex. Only the calling thread touches the
+    // component's vertices, queue slice and labels (components are disjoint), so plain loads and
+    // stores suffice. Visit stamps are negative: the level-synchronous sweeps use positive ones.
+
+    // One traversal from root with stamp `stamp`, the queue in q[0, z). Returns the eccentricity
+    // (-1 on a malformed row or a component larger than z); reached = vertices found; last_key =
+    // min (degree, id) key of the last level. q holds the Cuthill-McKee order from root.
+    __device__ int tiny_bfs(int root, int stamp, int* q, int z, int& reached, unsigned long long& last_key) const {
+        *vis_p(root) = stamp;
+        q[0] = root;
+        int head = 0, tail = 1, lend = 1, ecc = 0;
+        unsigned long long lmin = kKeyMax;
+        while (true) {
+            const int u = q[head++];
+            int r[8];
+            load_row(u, r);
+            const int d = r[7];
+            lmin = min(lmin, pack_key(d, u));
+#pragma unroll
+            for (int k = 0; k < kEllNb; ++k) {
+                if (k < d) {
+                    const int w = r[k];
+                    if (!in_graph(w)) return -1;
+                    if (*vis_p(w) != stamp) {
+                        if (tail >= z) return -1;
+                        *vis_p(w) = stamp;
+                        q[tail++] = w;
+                        if constexpr (!kSmem) asm volatile("prefetch.global.L1 [%0];" ::"l"(a->ell + 2 * (size_t)w));
+                    }
+                }
+            }
+            if (d > kEllNb) {
+                const int* row = a->adj + __ldg(a->rowptr + u);
+                for (int k = kEllNb; k < d; ++k) {
+                    const int w = __ldg(row + k);
+                    if (!in_graph(w)) return -1;
+                    if (*vis_p(w) != stamp) {
+                        if (tail >= z) return -1;
+                        *vis_p(w) = stamp;
+                        q[tail++] = w;
+                    }
+                }
+            }
+            if (head == lend) {
+                if (tail == lend) break;  // the level just dequeued was the last
+                ++ecc;
+                lend = tail;
+                lmin = kKeyMax;
+            }
+        }
+        reached = tail;
+        last_key = lmin;
+        return ecc;
+    }
+
+    // Orders the component of table entry t = (start vertex, first label, size, -) by the calling
+    // thread alone: Alg. 2's sweeps from the start vertex while the eccentricity grows strictly,
+    // then the last root's traversal is the numbering. q: the component's queue slice (t.z ints).
+    // Statistics go to st (shared or global, added atomically). Returns false on a failure, with
+    // the status set.
+    __device__ bool order_tiny(const int4& t, int* q, long long* st) {
+        const int z = t.z, y = t.y;
+        int stamp = -1, reached = 0;
+        unsigned long long k;
+        int ecc_prev = tiny_bfs(t.x, stamp--, q, z, reached, k);
+        if (ecc_prev < 0 || reached != z) {
+            fail_at(kSiteSize, t.x);
+            return false;
+        }
+        long long sweeps = 1, levels = ecc_prev + 1;
+        int ecc;
+        while (true) {
+            const int r = (int)(unsigned)(k & 0xffffffffu);
+            ecc = tiny_bfs(r, stamp--, q, z, reached, k);
+            if (ecc < 0 || reached != z) {
+                fail_at(kSiteSize, r);
+                return false;
+            }
+            ++sweeps;
+            levels += ecc + 1;
+            if (ecc <= ecc_prev) break;
+            ecc_prev = ecc;
+        }
+        // q[0, z) is the Cuthill-McKee order from the last root: labels y .. y + z - 1, reversed
+        const int n = a->n;
+        for (int i = 0; i < z; ++i) a->perm[n - 1 - (y + i)] = q[i];
+        // the same accounting as component(): without fused sweeps the numbering is one more
+        // traversal after the last sweep
+        const long long trav = a->fused ? sweeps : sweeps + 1;
+        if (!a->fused) levels += ecc + 1;
+        atomicAdd((unsigned long long*)&st[kStSweeps], (unsigned long long)sweeps);
+        atomicAdd((unsigned long long*)&st[kStTraversals], (unsigned long long)trav);
+        atomicAdd((unsigned long long*)&st[kStLevels], (unsigned long long)levels);
+        atomicAdd((unsigned long long*)&st[kStComponents], 1ull);
+        atomicMax((unsigned long long*)&st[kStMaxEcc], (unsigned long long)ecc);
         return true;
     }
 
@@ -1870,8 +1982,23 @@ struct Engine {
                 const int C = cc_prepare(nv, sm_sort, sm_sort_cap);
                 if (C == -2) return false;
                 if (C > 0) {
+                    if constexpr (!kSmem) {
+                        // tiny components first, one per thread, all at once
+                        for (int i = threadIdx.x; i < C; i += blockDim.x) {
+                            const int4 t = a->cc_tab[i];
+                            if (t.z > kTinyMax) continue;
+                            if (!tab_ok(t, nv)) {
+                                fail_at(kSiteTable, i);
+                                break;
+                            }
+                            if (!order_tiny(t, a->qa + t.y, sm->st)) break;
+                        }
+                        __syncthreads();
+                        if (ld_volatile(a->status) & (kErrInternal | kErrTimeout | kErrTooLarge)) return false;
+                    }
                     for (int i = 0; i < C; ++i) {
                         const int4 t = a->cc_tab[i];
+                        if (!kSmem && t.z <= kTinyMax) continue;
                         if (!tab_ok(t, nv)) {
                             fail_at(kSiteTable, i);
                             return false;

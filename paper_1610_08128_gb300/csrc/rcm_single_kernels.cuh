@@ -108,6 +108,16 @@ __device__ __forceinline__ void single_run(const EngineArgs& args, int stall, En
         for (int i = 0; i < 8; ++i) ctl->phase_ns[i] = smem.prof[i];
     }
     if (C <= 0) return;
+    // tiny components, one per thread of the grid, all at once
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < C; i += gridDim.x * blockDim.x) {
+        const int4 t = __ldcg(args.cc_tab + i);
+        if (t.z > kTinyMax || t.z >= args.cc_big) continue;
+        if (!e.tab_ok(t, nv)) {
+            e.fail_at(kSiteTable, i);
+            break;
+        }
+        if (!e.order_tiny(t, args.qa + t.y, ctl->stats)) break;
+    }
     // the other components, one per CTA (CTA barriers only)
     __syncthreads();
     Engine<true> ec;
@@ -123,7 +133,7 @@ __device__ __forceinline__ void single_run(const EngineArgs& args, int stall, En
             e.fail_at(kSiteTable, i);
             return;
         }
-        if (t.z >= args.cc_big) continue;
+        if (t.z >= args.cc_big || t.z <= kTinyMax) continue;
         EngineArgs ca = args;
         ca.qa = args.qa + t.y;
         ca.qb = args.qb + t.y;

@@ -140,6 +140,79 @@ def test_components_concurrent_with_a_grid_sized_one():
     assert_parity(synth.permute(synth.Csr(g2.n, g2.rowptr, g2.colidx), synth.random_permutation(g2.n, 64)))
 
 
+def tiny_mix(seed, big=(60, 50), count=300):
+    """One mid-sized grid plus a few hundred components of 2 to 40 vertices (paths, stars whose
+    centre row is longer than the padded row, cycles, random connected graphs, small grids;
+    sizes on both sides of the one-thread limit of 32) and isolated vertices; ids permuted and
+    rows stored in shuffled order."""
+    rng = synth.rng_for(seed)
+    parts = [synth.grid(big, seed=[seed, 0])] if big else []
+    for i in range(count):
+        z = int(rng.integers(2, 41))
+        kind = i % 5
+        if kind == 0:
+            g = synth.path(z, seed=[seed, i])
+        elif kind == 1:
+            g = synth.csr_from_edges(z, np.zeros(z - 1, np.int64), np.arange(1, z))
+        elif kind == 2:
+            g = synth.circulant(z, [1], seed=[seed, i]) if z >= 3 else synth.path(z)
+        elif kind == 3:
+            g = synth.random_graph(z, int(rng.integers(z - 1, 3 * z)), [seed, i], connected=True)
+        else:
+            a = max(1, int(np.sqrt(z)))
+            g = synth.grid((a, max(1, z // a)), seed=[seed, i])
+        parts.append(g)
+    parts.append(synth.csr_from_edges(25, [], []))
+    b = synth.concat(parts)
+    g = synth.Csr(b.n, b.rowptr, b.colidx)
+    return synth.shuffle_rows(synth.permute(g, synth.random_permutation(g.n, [seed, 1])), [seed, 2])
+
+
+def test_tiny_components_one_per_thread():
+    """Components of at most 32 vertices are ordered by one thread each (serial sweeps and
+    numbering from the sorted rows); larger ones by the CTA or grid engines. Every executor and
+    sweep mode gives the oracle's order, and the statistics count the same sweeps."""
+    for seed in (171, 172):
+        g = tiny_mix(seed)
+        want, ost = oracle.rcm(g.n, g.rowptr, g.colidx, with_stats=True)
+        for opts in ({}, {"executor": 1}, {"executor": 1, "fused_sweeps": -1}, {"executor": 1, "fused_sweeps": 2},
+                     {"executor": 1, "narrow_threshold": -1}):
+            got, st = gpu_perm(g, opts, with_stats=True)
+            assert np.array_equal(got, want), opts
+            # isolated vertices are numbered without sweeps; Alg. 2 on one vertex takes two
+            sweeps = ost["sweeps"] - 2 * ost["isolated"]
+            assert st["components"] == ost["components"] and st["sweeps"] == sweeps, opts
+            assert st["max_ecc"] == ost["max_ecc"], opts
+            if opts.get("fused_sweeps") == -1:
+                assert st["traversals"] == sweeps + ost["components"] - ost["isolated"], opts
+            else:
+                assert st["traversals"] == sweeps, opts
+    small = tiny_mix(173, big=None, count=150)       # small components only (the shared-memory CTA)
+    assert small.n <= 4608
+    assert_parity(small)
+    assert_parity(small, {"executor": 2, "block_threads": 64})
+
+
+def test_tiny_components_in_the_batch():
+    """The batched engine orders each graph's tiny components one per thread."""
+    rcm = rcm_mod()
+    graphs = [tiny_mix(181), tiny_mix(182, big=(9, 7)), tiny_mix(183, big=None), synth.knn_mesh(19000, 3, 184)]
+    b = synth.concat(graphs)
+    goff = torch.from_numpy(b.goff).cuda()
+    rp = torch.from_numpy(b.rowptr).cuda()
+    ci = torch.from_numpy(b.colidx).cuda()
+    want = [oracle.rcm(g.n, g.rowptr, g.colidx) for g in graphs]
+    for threads in (128, 256, 512):
+        o = rcm.rcm_batch_options()
+        o.block_threads = threads
+        perm = torch.full((b.n,), -1, dtype=torch.int32, device="cuda")
+        rcm.check(rcm.rcm_order_batch_ex(len(graphs), b.n, goff, rp, ci, perm, o), "batch_ex")
+        rcm.check(rcm.rcm_stream_status(), "batch_ex")
+        host = perm.cpu().numpy()
+        for gi in range(len(graphs)):
+            assert np.array_equal(host[b.goff[gi]:b.goff[gi + 1]], want[gi]), (threads, gi)
+
+
 def golden(name):
     """A pattern from tests/golden (explicit stored rows, or an edge list) and its expected perm."""
     import os
