@@ -116,6 +116,7 @@ struct EngineSmem {
     int bc[8];
     unsigned long long bck;
     int tail;
+    int ntail[3];                // narrow levels-only loop: new-vertex counters, by level mod 3
     int aflag;                   // async sweep: stop flag relayed to the CTA's warps
     // middle tier: this CTA's part of each cluster exchange, read by the cluster's CTAs through
     // distributed shared memory; double-buffered by epoch parity
@@ -558,6 +559,84 @@ struct Engine {
         accumulate(cnt, key);
     }
 
+    // Levels-only level run by one CTA alone (CTA 0 of the grid, or a CTA engine): the order of a
+    // levels-only frontier does not matter, so each warp reserves its new vertices' positions with
+    // one shared-memory atomic on *tail, which ends as the level's count. No CTA barrier and no
+    // (degree, id) minimum: the caller takes the minimum over the last level only.
+    __device__ void expand_narrow(int s, const int* cur, const int* cache, int F, int* nxt, int* ncache, int* tail) {
+        const int T = blockDim.x, lane = threadIdx.x & 31;
+        for (int i0 = 0; i0 < F; i0 += T) {
+            const int i = i0 + (int)threadIdx.x;
+            unsigned mask = 0;
+            int r[8];
+            int d = 0, u = -1;
+            if (i < F) {
+                u = cache ? cache[i] : ldcg(cur + i);
+                if (!in_graph(u)) {
+                    fail(kErrInternal);
+                    u = -1;
+                } else {
+                    load_row(u, r);
+                    d = r[7];
+                    int old[kEllNb];
+#pragma unroll
+                    for (int k = 0; k < kEllNb; ++k) old[k] = k < d ? atomicExch(vis_p(r[k]), s) : s;
+#pragma unroll
+                    for (int k = 0; k < kEllNb; ++k) mask |= (old[k] != s ? 1u : 0u) << k;
+                }
+            }
+            for_long_rows(u >= 0, u, d, [&](int, int w) {
+                const bool fresh = w >= 0 && atomicExch(vis_p(w), s) != s;
+                const unsigned bal = __ballot_sync(0xffffffffu, fresh);
+                if (bal) {
+                    int base = 0;
+                    if (lane == 0) base = atomicAdd(tail, __popc(bal));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (fresh) {
+                        const int pos = base + __popc(bal & ((1u << lane) - 1u));
+                        prefetch_row(w);
+                        nxt[pos] = w;
+                        if (ncache && pos < kCache) ncache[pos] = w;
+                    }
+                }
+                return false;
+            });
+            const int c = __popc(mask);
+            const int incl = warp_incl_scan(c);
+            const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+            if (wtot) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(tail, wtot);
+                int pos = __shfl_sync(0xffffffffu, base, 0) + incl - c;
+#pragma unroll
+                for (int k = 0; k < kEllNb; ++k)
+                    if (mask & (1u << k)) {
+                        prefetch_row(r[k]);
+                        nxt[pos] = r[k];
+                        if (ncache && pos < kCache) ncache[pos] = r[k];
+                        ++pos;
+                    }
+            }
+        }
+    }
+
+    // Min (degree, id) key over a level of F vertices held in cache (shared) or cur (global), for
+    // every thread of the CTA: Alg. 2's next root is the least such vertex of the last level.
+    __device__ unsigned long long level_min_key(const int* cur, const int* cache, int F) {
+        unsigned long long key = kKeyMax;
+        for (int i = threadIdx.x; i < F; i += blockDim.x) {
+            const int u = cache ? cache[i] : ldcg(cur + i);
+            if (!in_graph(u)) {
+                fail(kErrInternal);
+                continue;
+            }
+            int r[8];
+            load_row(u, r);
+            key = min(key, pack_key(r[7], u));
+        }
+        return block_min_u64(key, sm->wkey);
+    }
+
     // ---------------- bottom-up expansion (whole grid) ----------------
     // Top-down, a level's frontier pushes to its neighbours. Bottom-up, every vertex not yet reached
     // looks at its own neighbours instead. An unvisited vertex has no neighbour in a level below
@@ -912,21 +991,22 @@ struct Engine {
                         for (int i = threadIdx.x; i < F; i += blockDim.x) sm->cache[cb][i] = ldcg(cur + i);
                         in_cache = true;
                     }
+                    // one CTA barrier per level: the level's new-vertex counter is ntail[p], and the
+                    // next level's is cleared while this one runs (its last readers finished before
+                    // the previous level's barrier)
+                    int p = 0;
+                    if (threadIdx.x == 0) sm->ntail[0] = 0;
                     __syncthreads();
                     while (true) {
-                        if (threadIdx.x == 0) sm->tail = 0;
-                        __syncthreads();
-                        expand_levels(s, cur, F <= kCache ? sm->cache[cb] : nullptr, 0, F, nxt, sm->cache[cb ^ 1],
-                                      &sm->tail);
+                        if (threadIdx.x == 0) sm->ntail[p == 2 ? 0 : p + 1] = 0;
+                        const int* cache = F <= kCache ? sm->cache[cb] : nullptr;
+                        expand_narrow(s, cur, cache, F, nxt, sm->cache[cb ^ 1], &sm->ntail[p]);
                         __syncthreads();
                         tick(kPhExpand);
-                        const int cnt = sm->acc_cnt;
-                        const unsigned long long key = cta_key();
-                        __syncthreads();
-                        if (threadIdx.x == 0) sm->acc_cnt = 0;
+                        const int cnt = sm->ntail[p];
                         stat_add(kStNarrow, 1);
                         if (cnt == 0) {
-                            lk = key;
+                            lk = level_min_key(cur, cache, F);
                             F = 0;
                             break;
                         }
@@ -934,6 +1014,7 @@ struct Engine {
                         cb ^= 1;
                         F = cnt;
                         reached += cnt;
+                        p = p == 2 ? 0 : p + 1;
                         if (++ecc > a->n) {
                             fail_at(kSiteLevels, ecc);
                             return false;
@@ -1109,7 +1190,8 @@ struct Engine {
 
     // Phase A over a slice whose element j has key level_key(d, ord0 + j). Accumulates the min
     // (degree, id) over the slice. The round-0 row stays in (u0, r0) for phase B.
-    __device__ void phase_a(int d, unsigned long long ord0, const Slice& s, int& u0, int (&r0)[8]) {
+    __device__ void phase_a(int d, unsigned long long ord0, const Slice& s, int& u0, int (&r0)[8],
+                            bool with_key = true) {
         const int T = blockDim.x;
         unsigned long long mk = kKeyMax;
         u0 = -1;
@@ -1146,7 +1228,7 @@ struct Engine {
                 return false;
             });
         }
-        accumulate(0, mk);
+        if (with_key) accumulate(0, mk);
     }
 
     // Phase B over the same slice: the children each vertex owns, in key order then row order
@@ -1277,6 +1359,22 @@ struct Engine {
         return carry;
     }
 
+    // Min (degree, id) key over a slice, for every thread of the CTA (the last level of a narrow run).
+    __device__ unsigned long long slice_min_key(const Slice& s) {
+        unsigned long long key = kKeyMax;
+        for (int j = threadIdx.x; j < s.cnt; j += blockDim.x) {
+            const int u = sid(s, j);
+            if (!in_graph(u)) {
+                fail(kErrInternal);
+                continue;
+            }
+            int r[8];
+            load_row(u, r);
+            key = min(key, pack_key(r[7], u));
+        }
+        return block_min_u64(key, sm->wkey);
+    }
+
     // perm[n-1-(first+j)] = slice element j.
     __device__ void write_labels(const Slice& s, int first) {
         const int n = a->n;
@@ -1341,12 +1439,11 @@ struct Engine {
                     while (true) {
                         int u0;
                         int r0[8];
-                        phase_a(d, 0, cur, u0, r0);
+                        // no (degree, id) minimum per level: it is taken over the last level only
+                        phase_a(d, 0, cur, u0, r0, false);
+                        if (threadIdx.x == 0) sm->tail = 0;  // read by thread 0 alone, in phase_b
                         __syncthreads();
                         tick(kPhClaim);
-                        const unsigned long long key = cta_key();
-                        if (threadIdx.x == 0) sm->tail = 0;
-                        __syncthreads();
                         Slice nxt;
                         int* stage = (d & 1) ? a->qa : a->qb;
                         const int kids = phase_b(d, 0, cur, u0, r0, sm->cache[cb ^ 1], stage, &sm->tail,
@@ -1354,7 +1451,7 @@ struct Engine {
                         tick(kPhOwn);
                         stat_add(kStNarrow, 1);
                         if (kids == 0) {
-                            lk = key;
+                            lk = slice_min_key(cur);
                             lastF = F;
                             F = 0;
                             break;
@@ -1647,8 +1744,9 @@ struct Engine {
     // One connected component: sweeps from its start vertex r (Alg. 2), labelled traversal
     // (Alg. 3) with labels from nv. On return, size = the component's vertex count. With
     // all_left >= 0 (the number of vertices not yet numbered), the call stops after the first
-    // sweep when the component is smaller than that and small enough for the component table to
-    // order it at least as fast, returning size = -1 (nothing numbered).
+    // sweep when the component is smaller than that, is small enough for the component table to
+    // order it at least as fast, and holds less than 3/4 of the vertices left, returning
+    // size = -1 (nothing numbered).
     __device__ bool component(int r, int nv, int& size, long long all_left = -1) {
         if (!in_graph(r) || nv < 0 || nv >= a->n) {
             fail_at(kSiteStart, r);
@@ -1671,11 +1769,13 @@ struct Engine {
             return false;
         }
         // The start vertex's component does not hold every vertex left: the others get a component
-        // table. A component the table would order no faster (the grid's share for the whole grid;
-        // a CTA's beyond the one-thread limit) is finished here, its sweep kept: it takes the first
-        // labels either way. A smaller one is left to the table, its sweep discarded.
+        // table. The component is finished here, its sweep kept, when the table would order it no
+        // faster (the whole grid's size on the grid; beyond the one-thread limit on a CTA) or when
+        // it holds at least 3/4 of the vertices left (the rest, ordered concurrently afterwards,
+        // costs less than the sweep would again): it takes the first labels either way. Otherwise
+        // it is left to the table, to run beside the others, and its sweep is discarded.
         const long long keep_min = !kCtaOnly ? (long long)a->cc_big : (kSmem ? 0 : (long long)kTinyMax + 1);
-        if (all_left >= 0 && reached < all_left && reached < keep_min) {
+        if (all_left >= 0 && reached < all_left && reached < keep_min && 4 * reached < 3 * all_left) {
             size = -1;
             return true;
         }
