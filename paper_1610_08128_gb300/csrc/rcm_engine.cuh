@@ -51,6 +51,7 @@ namespace rcm {
 constexpr int kEllNb = 7;       // neighbours stored in a vertex's 32-byte row; slot 7 = degree
 constexpr int kCache = 2048;    // frontier ids cached in shared memory per buffer
 constexpr int kTinyMax = 32;    // components of at most this many vertices are ordered by one thread
+constexpr int kWarpLevel = 32;  // narrow levels of at most this many vertices run on warp 0 alone
 constexpr unsigned long long kClaimNone = ~0ull;
 
 struct EngineArgs {
@@ -117,6 +118,11 @@ struct EngineSmem {
     unsigned long long bck;
     int tail;
     int ntail[3];                // narrow levels-only loop: new-vertex counters, by level mod 3
+    struct {                     // state after a run of warp-0 levels, read by the whole CTA
+        int F, d, lstart, cb, lastF, bad, qb;
+        long long reached;
+        unsigned long long lk;
+    } wr;
     int aflag;                   // async sweep: stop flag relayed to the CTA's warps
     // middle tier: this CTA's part of each cluster exchange, read by the cluster's CTAs through
     // distributed shared memory; double-buffered by epoch parity
@@ -145,6 +151,18 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
 // the arguments provide it. kBottomUp (whole-grid engine only): each whole-grid level may run
 // bottom-up, chosen per level. Separate instantiations, so the plain top-down kernels carry none
 // of their code or registers.
+template <bool kCtaOnly, bool kSmem, bool kAsync, bool kBottomUp>
+struct Engine;
+
+// The warp-0 runs of narrow levels, kept out of line: they are entered once per run of levels, and
+// inlined they would raise every engine kernel's register pressure.
+template <bool kCtaOnly, bool kSmem, bool kAsync, bool kBottomUp>
+__device__ __noinline__ void run_warp_levels(const EngineArgs* a, EngineSmem* sm, int s, int F, int cb, int* cur,
+                                             int* nxt, int ecc, long long reached);
+template <bool kCtaOnly, bool kSmem, bool kAsync, bool kBottomUp>
+__device__ __noinline__ void run_warp_labelled(const EngineArgs* a, EngineSmem* sm, int d, int lstart, int F, int cb,
+                                               const int* sh, const int* g, int step);
+
 template <bool kCtaOnly, bool kSmem = false, bool kAsync = false, bool kBottomUp = false>
 struct Engine {
     static_assert(kCtaOnly || !kSmem, "shared-memory state needs a CTA engine");
@@ -557,6 +575,94 @@ struct Engine {
             cnt += c;
         }
         accumulate(cnt, key);
+    }
+
+    // Levels-only levels of at most kWarpLevel vertices, run by warp 0 alone (one vertex per lane,
+    // the frontier in the shared cache): positions come from a warp scan, the only synchronisation
+    // is __syncwarp, and the rows held in registers give the (degree, id) minimum of the last level.
+    // Runs while the levels stay that narrow (and, on the grid, below the narrow threshold); lane 0
+    // leaves the state in sm->wr. Called by the 32 threads of warp 0 only.
+    __device__ void warp_levels(int s, int F, int cb, int* cur, int* nxt, int ecc, long long reached) {
+        const int lane = threadIdx.x & 31;
+        unsigned long long lk = kKeyMax;
+        int bad = 0;
+        while (true) {
+            int* nc = sm->cache[cb ^ 1];
+            int cnt = 0;
+            unsigned long long m = kKeyMax;
+            unsigned mask = 0;
+            int r[8];
+            int d = 0, u = -1;
+            if (lane < F) {
+                u = sm->cache[cb][lane];
+                if (!in_graph(u)) {
+                    bad = 1;
+                    u = -1;
+                } else {
+                    load_row(u, r);
+                    d = r[7];
+                    m = pack_key(d, u);
+                    int old[kEllNb];
+#pragma unroll
+                    for (int k = 0; k < kEllNb; ++k) old[k] = k < d ? atomicExch(vis_p(r[k]), s) : s;
+#pragma unroll
+                    for (int k = 0; k < kEllNb; ++k) mask |= (old[k] != s ? 1u : 0u) << k;
+                }
+            }
+            for_long_rows(u >= 0, u, d, [&](int, int w) {
+                const bool fresh = w >= 0 && atomicExch(vis_p(w), s) != s;
+                const unsigned bal = __ballot_sync(0xffffffffu, fresh);
+                if (fresh) {
+                    const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+                    prefetch_row(w);
+                    nxt[pos] = w;
+                    if (pos < kCache) nc[pos] = w;
+                }
+                cnt += __popc(bal);
+                return false;
+            });
+            const int cc = __popc(mask);
+            const int incl = warp_incl_scan(cc);
+            int pos = cnt + incl - cc;
+#pragma unroll
+            for (int k = 0; k < kEllNb; ++k)
+                if (mask & (1u << k)) {
+                    prefetch_row(r[k]);
+                    nxt[pos] = r[k];
+                    if (pos < kCache) nc[pos] = r[k];
+                    ++pos;
+                }
+            cnt += __shfl_sync(0xffffffffu, incl, 31);
+            __syncwarp();
+            tick(kPhExpand);
+            stat_add(kStNarrow, 1);
+            if (cnt == 0) {
+                lk = warp_min_u64(m);
+                F = 0;
+                break;
+            }
+            int* t = cur; cur = nxt; nxt = t;
+            cb ^= 1;
+            F = cnt;
+            reached += cnt;
+            if (++ecc > a->n) {
+                if (lane == 0) fail_at(kSiteLevels, ecc);
+                bad = 1;
+                break;
+            }
+            if (F > kWarpLevel || (!kCtaOnly && F >= a->narrow_thr)) break;
+        }
+        bad = __any_sync(0xffffffffu, bad) ? 1 : 0;
+        if (lane == 0) {
+            if (bad) fail(kErrInternal);
+            sm->wr.F = F;
+            sm->wr.cb = cb;
+            sm->wr.d = ecc;
+            sm->wr.reached = reached;
+            sm->wr.lk = lk;
+            sm->wr.bad = bad;
+            sm->wr.qb = cur == a->qb ? 1 : 0;
+        }
     }
 
     // Levels-only level run by one CTA alone (CTA 0 of the grid, or a CTA engine): the order of a
@@ -998,6 +1104,27 @@ struct Engine {
                     if (threadIdx.x == 0) sm->ntail[0] = 0;
                     __syncthreads();
                     while (true) {
+                        // a run of narrow levels on warp 0 (the shared-memory CTA only: in the other
+                        // engines the extra code cost more through register allocation than it saved);
+                        // ntail[p] stays clear for the next CTA level
+                        if (kSmem && F <= kWarpLevel) {
+                            if (threadIdx.x < 32)
+                                run_warp_levels<kCtaOnly, kSmem, kAsync, kBottomUp>(a, sm, s, F, cb, cur, nxt, ecc, reached);
+                            __syncthreads();
+                            F = sm->wr.F;
+                            cb = sm->wr.cb;
+                            ecc = sm->wr.d;
+                            reached = sm->wr.reached;
+                            if (sm->wr.bad) return false;
+                            cur = sm->wr.qb ? a->qb : a->qa;
+                            nxt = sm->wr.qb ? a->qa : a->qb;
+                            if (F == 0) {
+                                lk = sm->wr.lk;
+                                break;
+                            }
+                            if (!kCtaOnly && F >= a->narrow_thr) break;
+                            continue;
+                        }
                         if (threadIdx.x == 0) sm->ntail[p == 2 ? 0 : p + 1] = 0;
                         const int* cache = F <= kCache ? sm->cache[cb] : nullptr;
                         expand_narrow(s, cur, cache, F, nxt, sm->cache[cb ^ 1], &sm->ntail[p]);
@@ -1375,6 +1502,127 @@ struct Engine {
         return block_min_u64(key, sm->wkey);
     }
 
+    // Labelled levels of at most kWarpLevel vertices, run by warp 0 alone (one vertex per lane):
+    // phase_a's claims and phase_b's ownership with a warp scan and __syncwarp instead of CTA scans
+    // and barriers, the row kept in registers between the two. Children take labels from
+    // lstart + F in (key, row) order and go to the shared cache as the next level (and to perm,
+    // which holds every level for the grid or a wider next level). Runs while the levels stay that
+    // narrow (and, on the grid, below the narrow threshold); lane 0 leaves the state in sm->wr
+    // (F = 0: the sweep ended with the level of lastF vertices at lstart, lk its least vertex key).
+    // Called by the 32 threads of warp 0 only.
+    __device__ void warp_labelled(int d, int lstart, int F, int cb, Slice cur) {
+        const int lane = threadIdx.x & 31;
+        const int n = a->n;
+        const unsigned lt = (1u << lane) - 1u;
+        unsigned long long lk = kKeyMax;
+        int lastF = 0, bad = 0;
+        while (true) {
+            int u = -1, dg = 0;
+            int rw[8];
+            unsigned long long key = 0;
+            // phase A: every neighbour's claim lowered to this vertex's key
+            if (lane < F) {
+                const int v = sid(cur, lane);
+                if (!in_graph(v)) {
+                    bad = 1;
+                } else {
+                    u = v;
+                    load_row(v, rw);
+                    dg = rw[7];
+                    key = level_key(d, (unsigned long long)lane);
+#pragma unroll
+                    for (int k = 0; k < kEllNb; ++k)
+                        if (k < dg) atomicMin(claim_p(rw[k]), key);
+                }
+            }
+            for_long_rows(u >= 0, u, dg, [&](int src, int w) {
+                const unsigned long long kk = __shfl_sync(0xffffffffu, key, src);
+                if (w >= 0) atomicMin(claim_p(w), kk);
+                return false;
+            });
+            __syncwarp();
+            tick(kPhClaim);
+            // phase B: the children each vertex owns, counted, then numbered in (key, row) order
+            const unsigned mask = u >= 0 ? owned_mask(rw, dg, key) : 0u;
+            int cnt = __popc(mask);
+            for_long_rows(u >= 0, u, dg, [&](int src, int w) {
+                const unsigned long long kk = __shfl_sync(0xffffffffu, key, src);
+                const int m = __popc(__ballot_sync(0xffffffffu, w >= 0 && ld_claim(w) == kk));
+                if (lane == src) cnt += m;
+                return false;
+            });
+            const int incl = warp_incl_scan(cnt);
+            const int kids = __shfl_sync(0xffffffffu, incl, 31);
+            int q = incl - cnt;
+            int* nc = sm->cache[cb ^ 1];
+            const int lab0 = lstart + F;  // first label of the next level
+            if (u >= 0) {
+#pragma unroll
+                for (int k = 0; k < kEllNb; ++k)
+                    if (mask & (1u << k)) {
+                        const int w = rw[k];
+                        prefetch_row(w);
+                        if (q < kCache) nc[q] = w;
+                        const int lab = lab0 + q;
+                        if ((unsigned)lab < (unsigned)n) a->perm[n - 1 - lab] = w; else bad = 1;
+                        ++q;
+                    }
+            }
+            for_long_rows(u >= 0, u, dg, [&](int src, int w) {
+                const unsigned long long kk = __shfl_sync(0xffffffffu, key, src);
+                const bool own = w >= 0 && ld_claim(w) == kk;
+                const unsigned bal = __ballot_sync(0xffffffffu, own);
+                const int base = __shfl_sync(0xffffffffu, q, src);
+                if (own) {
+                    const int qq = base + __popc(bal & lt);
+                    prefetch_row(w);
+                    if (qq < kCache) nc[qq] = w;
+                    const int lab = lab0 + qq;
+                    if ((unsigned)lab < (unsigned)n) a->perm[n - 1 - lab] = w; else bad = 1;
+                }
+                if (lane == src) q += __popc(bal);
+                return false;
+            });
+            __syncwarp();
+            tick(kPhOwn);
+            stat_add(kStNarrow, 1);
+            if (kids == 0) {
+                lk = warp_min_u64(u >= 0 ? pack_key(dg, u) : kKeyMax);
+                lastF = F;
+                F = 0;
+                break;
+            }
+            lstart += F;
+            F = kids;
+            cb ^= 1;
+            if (F <= kCache) {
+                cur.sh = sm->cache[cb];
+                cur.g = nullptr;
+                cur.step = 1;
+                cur.cnt = F;
+            } else {
+                cur = perm_range(lstart, F);
+            }
+            if (++d > n) {
+                if (lane == 0) fail_at(kSiteLevels, d);
+                bad = 1;
+                break;
+            }
+            if (F > kWarpLevel || (!kCtaOnly && F >= a->narrow_thr)) break;
+        }
+        bad = __any_sync(0xffffffffu, bad) ? 1 : 0;
+        if (lane == 0) {
+            if (bad) fail(kErrInternal);
+            sm->wr.F = F;
+            sm->wr.d = d;
+            sm->wr.lstart = lstart;
+            sm->wr.cb = cb;
+            sm->wr.lastF = lastF;
+            sm->wr.lk = lk;
+            sm->wr.bad = bad;
+        }
+    }
+
     // perm[n-1-(first+j)] = slice element j.
     __device__ void write_labels(const Slice& s, int first) {
         const int n = a->n;
@@ -1437,6 +1685,32 @@ struct Engine {
                 int lastF = 0;
                 if (kCtaOnly || b == 0) {
                     while (true) {
+                        if (kSmem && F <= kWarpLevel) {
+                            // a run of narrow levels on warp 0 (the shared-memory CTA only, as above)
+                            if (threadIdx.x < 32)
+                                run_warp_labelled<kCtaOnly, kSmem, kAsync, kBottomUp>(a, sm, d, lstart, F, cb, cur.sh, cur.g, cur.step);
+                            __syncthreads();
+                            F = sm->wr.F;
+                            d = sm->wr.d;
+                            lstart = sm->wr.lstart;
+                            cb = sm->wr.cb;
+                            if (sm->wr.bad) return false;
+                            if (F == 0) {
+                                lk = sm->wr.lk;
+                                lastF = sm->wr.lastF;
+                                break;
+                            }
+                            if (F <= kCache) {
+                                cur.sh = sm->cache[cb];
+                                cur.g = nullptr;
+                                cur.step = 1;
+                                cur.cnt = F;
+                            } else {
+                                cur = perm_range(lstart, F);
+                            }
+                            if (!kCtaOnly && F >= a->narrow_thr) break;
+                            continue;
+                        }
                         int u0;
                         int r0[8];
                         // no (degree, id) minimum per level: it is taken over the last level only
@@ -2131,5 +2405,28 @@ struct Engine {
         return true;
     }
 };
+
+template <bool kCtaOnly, bool kSmem, bool kAsync, bool kBottomUp>
+__device__ __noinline__ void run_warp_levels(const EngineArgs* a, EngineSmem* sm, int s, int F, int cb, int* cur,
+                                             int* nxt, int ecc, long long reached) {
+    Engine<kCtaOnly, kSmem, kAsync, kBottomUp> e;
+    e.a = a;
+    e.sm = sm;
+    e.warp_levels(s, F, cb, cur, nxt, ecc, reached);
+}
+
+template <bool kCtaOnly, bool kSmem, bool kAsync, bool kBottomUp>
+__device__ __noinline__ void run_warp_labelled(const EngineArgs* a, EngineSmem* sm, int d, int lstart, int F, int cb,
+                                               const int* sh, const int* g, int step) {
+    Engine<kCtaOnly, kSmem, kAsync, kBottomUp> e;
+    e.a = a;
+    e.sm = sm;
+    typename Engine<kCtaOnly, kSmem, kAsync, kBottomUp>::Slice cur;
+    cur.sh = sh;
+    cur.g = g;
+    cur.step = step;
+    cur.cnt = F;
+    e.warp_labelled(d, lstart, F, cb, cur);
+}
 
 }  // namespace rcm
