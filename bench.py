@@ -737,9 +737,11 @@ def main():
             "config": dict(cfg, parallelism="replicas" if world > 1 else "single", launch=tuned,
                            l2="inputs larger than L2, and a 2x-L2 buffer is written between steps"),
             "roofline": roofline, "roofline_expansion": roofline_expansion, "cpu_baseline": cpu, "e2e": e2e,
-            # per step: k_degree_validate, k_sort_rows_small, k_sort_rows_big, k_rcm_single, k_latch,
-            # and k_l2_release after a traversal with the L2 window
-            "gpu_launches": (6 if tuned.get("l2_persist", 0) > 0 else 5) * args.steps, "clocks": clocks,
+            # per step: k_degree_validate, k_sort_rows_small, k_sort_rows_big, k_rcm_single (or
+            # k_rcm_small), k_rcm_components after the persistent kernel, k_latch, and k_l2_release after
+            # a traversal with the L2 window
+            "gpu_launches": (5 + (tuned.get("executor", 0) != 2) + (tuned.get("l2_persist", 0) > 0)) * args.steps,
+            "clocks": clocks,
             "stats": dict(stats, prep_ms=statistics.mean(prep_ms), traverse_ms=trav),
             "quality": dict(qual, bandwidth=bw, profile=prof), "sort_free": sort_free,
             "configs": configs, "batched": batched, "served": served,

@@ -17,7 +17,7 @@ LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "librcm_gb300.so")
 SOURCES = [*(f"rcm_kern_grid{w}.cu" for w in (32, 64, 128, 256, 512, 1024)), "rcm_kern_grid512_async.cu",
            "rcm_kern_grid512_hybrid.cu",
-           "rcm_kern_small.cu",
+           "rcm_kern_small.cu", "rcm_kern_components.cu",
            "rcm_batch.cu", "rcm_capi.cu", "rcm_prep.cu", "rcm_single.cu", "rcm_server.cu", "rcm_validate.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Kernel templates are instantiated once, in their own translation units, and launched from the

@@ -144,6 +144,8 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// kWarp (CTA engines only; on by default with kSmem): narrow levels of at most kWarpLevel vertices
+// run on warp 0 alone. Off in the engines it slowed through register allocation.
 // kSmem (CTA engines only): the claims, visit stamps and padded rows of the graph live in shared
 // memory, indexed from the graph's first vertex v0; otherwise they are global arrays indexed by
 // vertex id.
@@ -151,21 +153,22 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
 // the arguments provide it. kBottomUp (whole-grid engine only): each whole-grid level may run
 // bottom-up, chosen per level. Separate instantiations, so the plain top-down kernels carry none
 // of their code or registers.
-template <bool kCtaOnly, bool kSmem, bool kAsync, bool kBottomUp>
+template <bool kCtaOnly, bool kSmem, bool kAsync, bool kBottomUp, bool kWarp>
 struct Engine;
 
 // The warp-0 runs of narrow levels, kept out of line: they are entered once per run of levels, and
 // inlined they would raise every engine kernel's register pressure.
-template <bool kCtaOnly, bool kSmem, bool kAsync, bool kBottomUp>
+template <bool kCtaOnly, bool kSmem, bool kAsync, bool kBottomUp, bool kWarp>
 __device__ __noinline__ void run_warp_levels(const EngineArgs* a, EngineSmem* sm, int s, int F, int cb, int* cur,
                                              int* nxt, int ecc, long long reached);
-template <bool kCtaOnly, bool kSmem, bool kAsync, bool kBottomUp>
+template <bool kCtaOnly, bool kSmem, bool kAsync, bool kBottomUp, bool kWarp>
 __device__ __noinline__ void run_warp_labelled(const EngineArgs* a, EngineSmem* sm, int d, int lstart, int F, int cb,
                                                const int* sh, const int* g, int step);
 
-template <bool kCtaOnly, bool kSmem = false, bool kAsync = false, bool kBottomUp = false>
+template <bool kCtaOnly, bool kSmem = false, bool kAsync = false, bool kBottomUp = false, bool kWarp = kSmem>
 struct Engine {
     static_assert(kCtaOnly || !kSmem, "shared-memory state needs a CTA engine");
+    static_assert(kCtaOnly || !kWarp, "warp-0 levels need a CTA engine");
     static_assert(!kAsync || !kCtaOnly, "asynchronous sweeps need the whole grid");
     static_assert(!kBottomUp || !kCtaOnly, "bottom-up levels need the whole grid");
     const EngineArgs* a;   // in shared memory (keeps the per-thread register footprint small)
@@ -1104,12 +1107,12 @@ struct Engine {
                     if (threadIdx.x == 0) sm->ntail[0] = 0;
                     __syncthreads();
                     while (true) {
-                        // a run of narrow levels on warp 0 (the shared-memory CTA only: in the other
-                        // engines the extra code cost more through register allocation than it saved);
+                        // a run of narrow levels on warp 0 (where kWarp is on: in the grid and batch
+                        // kernels the extra code cost more through register allocation than it saved);
                         // ntail[p] stays clear for the next CTA level
-                        if (kSmem && F <= kWarpLevel) {
+                        if (kWarp && F <= kWarpLevel) {
                             if (threadIdx.x < 32)
-                                run_warp_levels<kCtaOnly, kSmem, kAsync, kBottomUp>(a, sm, s, F, cb, cur, nxt, ecc, reached);
+                                run_warp_levels<kCtaOnly, kSmem, kAsync, kBottomUp, kWarp>(a, sm, s, F, cb, cur, nxt, ecc, reached);
                             __syncthreads();
                             F = sm->wr.F;
                             cb = sm->wr.cb;
@@ -1685,10 +1688,10 @@ struct Engine {
                 int lastF = 0;
                 if (kCtaOnly || b == 0) {
                     while (true) {
-                        if (kSmem && F <= kWarpLevel) {
-                            // a run of narrow levels on warp 0 (the shared-memory CTA only, as above)
+                        if (kWarp && F <= kWarpLevel) {
+                            // a run of narrow levels on warp 0 (where kWarp is on, as above)
                             if (threadIdx.x < 32)
-                                run_warp_labelled<kCtaOnly, kSmem, kAsync, kBottomUp>(a, sm, d, lstart, F, cb, cur.sh, cur.g, cur.step);
+                                run_warp_labelled<kCtaOnly, kSmem, kAsync, kBottomUp, kWarp>(a, sm, d, lstart, F, cb, cur.sh, cur.g, cur.step);
                             __syncthreads();
                             F = sm->wr.F;
                             d = sm->wr.d;
@@ -2406,22 +2409,22 @@ struct Engine {
     }
 };
 
-template <bool kCtaOnly, bool kSmem, bool kAsync, bool kBottomUp>
+template <bool kCtaOnly, bool kSmem, bool kAsync, bool kBottomUp, bool kWarp>
 __device__ __noinline__ void run_warp_levels(const EngineArgs* a, EngineSmem* sm, int s, int F, int cb, int* cur,
                                              int* nxt, int ecc, long long reached) {
-    Engine<kCtaOnly, kSmem, kAsync, kBottomUp> e;
+    Engine<kCtaOnly, kSmem, kAsync, kBottomUp, kWarp> e;
     e.a = a;
     e.sm = sm;
     e.warp_levels(s, F, cb, cur, nxt, ecc, reached);
 }
 
-template <bool kCtaOnly, bool kSmem, bool kAsync, bool kBottomUp>
+template <bool kCtaOnly, bool kSmem, bool kAsync, bool kBottomUp, bool kWarp>
 __device__ __noinline__ void run_warp_labelled(const EngineArgs* a, EngineSmem* sm, int d, int lstart, int F, int cb,
                                                const int* sh, const int* g, int step) {
-    Engine<kCtaOnly, kSmem, kAsync, kBottomUp> e;
+    Engine<kCtaOnly, kSmem, kAsync, kBottomUp, kWarp> e;
     e.a = a;
     e.sm = sm;
-    typename Engine<kCtaOnly, kSmem, kAsync, kBottomUp>::Slice cur;
+    typename Engine<kCtaOnly, kSmem, kAsync, kBottomUp, kWarp>::Slice cur;
     cur.sh = sh;
     cur.g = g;
     cur.step = step;

@@ -392,6 +392,16 @@ static cudaError_t release_persisting(const char* win, size_t bytes, cudaStream_
     return cudaLaunchKernelExC(&cfg, (const void*)k_l2_release, kargs);
 }
 
+// The components that the persistent kernel's component table leaves to smaller engines
+// (k_rcm_components): as many threads as the traversal had, in CTAs of kComponentThreads. The
+// kernel reads the table's size from the control block and exits at once when there is none.
+static cudaError_t launch_components(EngineArgs& args, const SingleLaunch& sl, cudaStream_t s) {
+    const int blocks = std::max(1, sl.blocks * sl.threads / kComponentThreads);
+    void* cargs[] = {&args};
+    return cudaLaunchKernel((const void*)k_rcm_components<kComponentThreads>, dim3(blocks), dim3(kComponentThreads),
+                            cargs, 0, s);
+}
+
 cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* colidx, int* perm, char* base,
                            const SingleLayout& L, const SingleLaunch& sl, cudaEvent_t* ev, cudaStream_t s) {
     const DeviceInfo& di = device_info();
@@ -498,6 +508,7 @@ cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* c
         e = cudaLaunchKernelExC(&cfg, single_kernel(sl.threads, async, hybrid), kargs);
     } else if (sl.l2_persist || sl.mid_k > 0) {
         e = launch_grid(single_kernel(sl.threads, async, hybrid), sl, kargs, base + L.claim, L.bigrows - L.claim, s);
+        if (e == cudaSuccess) e = launch_components(args, sl, s);
         if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
         if (e == cudaSuccess && sl.l2_persist) e = release_persisting(base + L.claim, L.bigrows - L.claim, s);
         return e;
@@ -505,6 +516,7 @@ cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* c
         e = cudaLaunchCooperativeKernel(single_kernel(sl.threads, async, hybrid), dim3(sl.blocks), dim3(sl.threads), kargs,
                                         kSingleDynSmem, s);
     }
+    if (e == cudaSuccess && !sl.small) e = launch_components(args, sl, s);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
     return e;
 }

@@ -28,6 +28,9 @@ template <int kThreads, bool kAsync, bool kBottomUp>
 __global__ void __launch_bounds__(kThreads, 1) k_rcm_single(EngineArgs args, int stall);
 template <int kThreads>
 __global__ void __launch_bounds__(kThreads, 1) k_rcm_small(EngineArgs args, int vis_off, int ell_off);
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads) k_rcm_components(EngineArgs args);
+constexpr int kComponentThreads = 256;  // CTA width of k_rcm_components
 
 #ifndef RCM_KERNEL_DEFINITIONS
 extern template __global__ void k_rcm_single<32, false, false>(EngineArgs, int);
@@ -43,6 +46,7 @@ extern template __global__ void k_rcm_small<64>(EngineArgs, int, int);
 extern template __global__ void k_rcm_small<128>(EngineArgs, int, int);
 extern template __global__ void k_rcm_small<256>(EngineArgs, int, int);
 extern template __global__ void k_rcm_small<512>(EngineArgs, int, int);
+extern template __global__ void k_rcm_components<kComponentThreads>(EngineArgs);
 #else
 template <int kThreads, bool kAsync, bool kBottomUp>
 __device__ __forceinline__ void single_run(const EngineArgs& args, int stall, EngineSmem& smem, int& s_item,
@@ -99,7 +103,7 @@ __device__ __forceinline__ void single_run(const EngineArgs& args, int stall, En
             }
         }
     }
-    // statistics: CTA 0 adds the grid part; CTAs add their own parts below (ctl->stats starts at 0)
+    // statistics: CTA 0 adds the grid part; k_rcm_components adds its own (ctl->stats starts at 0)
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         for (int i = 0; i < 8; ++i) {
             if (i == kStMaxEcc) atomicMax((unsigned long long*)&ctl->stats[i], (unsigned long long)smem.st[i]);
@@ -107,63 +111,10 @@ __device__ __forceinline__ void single_run(const EngineArgs& args, int stall, En
         }
         for (int i = 0; i < 8; ++i) ctl->phase_ns[i] = smem.prof[i];
     }
-    if (C <= 0) return;
-    // tiny components, one per thread of the grid, all at once
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < C; i += gridDim.x * blockDim.x) {
-        const int4 t = __ldcg(args.cc_tab + i);
-        if (t.z > kTinyMax || t.z >= args.cc_big) continue;
-        if (!e.tab_ok(t, nv)) {
-            e.fail_at(kSiteTable, i);
-            break;
-        }
-        if (!e.order_tiny(t, args.qa + t.y, ctl->stats)) break;
-    }
-    // the other components, one per CTA (CTA barriers only)
-    __syncthreads();
-    Engine<true> ec;
-    bool any = false;
-    while (true) {
-        if (threadIdx.x == 0) s_item = atomicAdd(&ctl->work_next, 1);
-        __syncthreads();
-        const int i = s_item;
-        __syncthreads();
-        if (i >= C) break;
-        const int4 t = __ldcg(args.cc_tab + i);
-        if (!e.tab_ok(t, nv)) {
-            e.fail_at(kSiteTable, i);
-            return;
-        }
-        if (t.z >= args.cc_big || t.z <= kTinyMax) continue;
-        EngineArgs ca = args;
-        ca.qa = args.qa + t.y;
-        ca.qb = args.qb + t.y;
-        ca.boff = args.boff + t.y;
-        ca.narrow_thr = 0x7fffffff;
-        ca.obits = claim_order_bits(t.z);
-        ca.profile = 0;
-        if (!any) {
-            ec.init(ca, &smem);
-            // visit stamps of these engines stay clear of the grid engine's (whose first sweep may
-            // already have stamped the first component)
-            ec.sweep_id = 1 << 24;
-            any = true;
-        } else {
-            __syncthreads();
-            if (threadIdx.x == 0) smem.args = ca;
-            __syncthreads();
-        }
-        int size;
-        if (!ec.component(t.x, t.y, size)) return;
-        if (size != t.z) {
-            ec.fail(kErrInternal);
-            return;
-        }
-    }
-    if (any && threadIdx.x == 0) {
-        for (int i = 0; i < 8; ++i) {
-            if (i == kStMaxEcc) atomicMax((unsigned long long*)&ctl->stats[i], (unsigned long long)smem.st[i]);
-            else if (i != kStIsolated && i != kStGrid) atomicAdd((unsigned long long*)&ctl->stats[i], (unsigned long long)smem.st[i]);
-        }
+    // the components smaller than the whole grid: k_rcm_components, launched after this kernel
+    if (C > 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->comp_count = C;
+        ctl->comp_nv = nv;
     }
 }
 
@@ -183,6 +134,73 @@ __global__ void __launch_bounds__(kThreads, 1) k_rcm_single(EngineArgs args, int
     if (args.mid_k > 0) cluster_barrier();
 }
 
+
+// The components that k_rcm_single's component table left to smaller engines: those of at most
+// kTinyMax vertices one per thread, the others (below the whole-grid size) one per CTA from a work
+// queue, with CTA barriers only and their levels of at most kWarpLevel vertices on warp 0. A kernel
+// of its own, so that neither its engine's code nor its CTA width weighs on the persistent grid
+// kernel. Exits at once when the ordering built no table.
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads) k_rcm_components(EngineArgs args) {
+    __shared__ EngineSmem smem;
+    __shared__ int s_item;
+    Ctl* ctl = args.ctl;
+    if (ld_volatile(&ctl->status) & (kErrBadCsr | kErrInternal | kErrTimeout | kErrTooLarge)) return;
+    const int C = ctl->comp_count, nv = ctl->comp_nv;  // written by the previous kernel on this stream
+    if (C <= 0) return;
+    Engine<true, false, false, false, true> e;
+    EngineArgs first = args;
+    first.narrow_thr = 0x7fffffff;
+    first.profile = 0;
+    e.init(first, &smem);
+    // visit stamps clear of the grid engine's (whose first sweep may have stamped a component)
+    e.sweep_id = 1 << 24;
+    // tiny components, one per thread of the grid, all at once
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < C; i += gridDim.x * blockDim.x) {
+        const int4 t = __ldcg(args.cc_tab + i);
+        if (t.z > kTinyMax || t.z >= args.cc_big) continue;
+        if (!e.tab_ok(t, nv)) {
+            e.fail_at(kSiteTable, i);
+            break;
+        }
+        if (!e.order_tiny(t, args.qa + t.y, ctl->stats)) break;
+    }
+    // the others, one per CTA
+    bool any = false;
+    while (true) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&ctl->work_next, 1);
+        __syncthreads();
+        const int i = s_item;
+        __syncthreads();
+        if (i >= C) break;
+        const int4 t = __ldcg(args.cc_tab + i);
+        if (t.z >= args.cc_big || t.z <= kTinyMax) continue;
+        if (!e.tab_ok(t, nv)) {
+            e.fail_at(kSiteTable, i);
+            return;
+        }
+        EngineArgs ca = first;
+        ca.qa = args.qa + t.y;
+        ca.qb = args.qb + t.y;
+        ca.boff = args.boff + t.y;
+        ca.obits = claim_order_bits(t.z);
+        if (threadIdx.x == 0) smem.args = ca;
+        __syncthreads();
+        any = true;
+        int size;
+        if (!e.component(t.x, t.y, size)) return;
+        if (size != t.z) {
+            e.fail(kErrInternal);
+            return;
+        }
+    }
+    if (any && threadIdx.x == 0) {
+        for (int i = 0; i < 8; ++i) {
+            if (i == kStMaxEcc) atomicMax((unsigned long long*)&ctl->stats[i], (unsigned long long)smem.st[i]);
+            else if (i != kStIsolated && i != kStGrid) atomicAdd((unsigned long long*)&ctl->stats[i], (unsigned long long)smem.st[i]);
+        }
+    }
+}
 
 // kThreads: narrow graphs (a few dozen vertices per level) run best on small CTAs, whose barriers,
 // scans and reductions are cheap.
