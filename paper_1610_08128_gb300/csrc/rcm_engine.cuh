@@ -2220,22 +2220,49 @@ struct Engine {
     __device__ int cc_prepare(int nv, unsigned long long* sort_smem, int sort_cap) {
         const int n = a->n, v0 = a->v0;
         int* counter = kCtaOnly ? &sm->bc[4] : &a->ctl->ncomp;
+        // the unnumbered vertices, compacted in the first pass so that the others run over them
+        // alone (after a first component that held most of the graph, a small fraction); the
+        // frontier queue is idle between components. The grid's counter starts at 0 (the control
+        // block is cleared per ordering, and this runs once per ordering).
+        int* list = a->qb;
+        int* lcount = kCtaOnly ? &sm->bc[5] : &a->ctl->cc_open;
         const int stride = cta_count() * blockDim.x;
-        const int first = cta_rank() * blockDim.x + threadIdx.x;
-        for (int i = first; i < n; i += stride) {
-            const int v = v0 + i;
-            if (ld_claim(v) == kClaimNone) {
-                a->cc_parent[v] = v;
-                a->cc_size[v] = 0;
-                a->cc_key[v] = kKeyMax;
-            }
+        const int lane = threadIdx.x & 31;
+        if (kCtaOnly) {
+            if (threadIdx.x == 0) *lcount = 0;
+            __syncthreads();
         }
-        if (cta_rank() == 0 && threadIdx.x == 0) *counter = 0;
-        if (!barrier()) return -2;
         for (int i0 = cta_rank() * blockDim.x; i0 < n; i0 += stride) {
             const int i = i0 + (int)threadIdx.x;
             const int v = v0 + i;
             const bool open = i < n && ld_claim(v) == kClaimNone;
+            if (open) {
+                a->cc_parent[v] = v;
+                a->cc_size[v] = 0;
+                a->cc_key[v] = kKeyMax;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, open);
+            if (bal) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(lcount, __popc(bal));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (open) list[base + __popc(bal & ((1u << lane) - 1u))] = v;
+            }
+        }
+        if (cta_rank() == 0 && threadIdx.x == 0) *counter = 0;
+        if (!barrier()) return -2;
+        if (threadIdx.x == 0) sm->bc[0] = kCtaOnly ? *lcount : ldcg(lcount);
+        __syncthreads();
+        const int L = sm->bc[0];
+        __syncthreads();
+        if (L > n) {
+            fail_at(kSiteTotal, L);
+            return -2;
+        }
+        for (int i0 = cta_rank() * blockDim.x; i0 < L; i0 += stride) {
+            const int i = i0 + (int)threadIdx.x;
+            const bool open = i < L;
+            const int v = open ? ldcg(list + i) : v0;
             int d = 0;
             if (open) {
                 int r[8];
@@ -2252,9 +2279,8 @@ struct Engine {
             });
         }
         if (!barrier()) return -2;
-        for (int i = first; i < n; i += stride) {
-            const int v = v0 + i;
-            if (ld_claim(v) != kClaimNone) continue;
+        for (int i = cta_rank() * blockDim.x + threadIdx.x; i < L; i += stride) {
+            const int v = ldcg(list + i);
             const int r = cc_root((volatile int*)a->cc_parent, v, v0, v0 + n);
             if (r < 0) fail_at(kSiteParent, v);
             if (r == v) {
@@ -2269,11 +2295,10 @@ struct Engine {
         __syncthreads();
         if (C > a->cc_cap) return -1;
         // sizes and start keys per root (lanes with the same root combine first)
-        const int lane = threadIdx.x & 31;
-        for (int i0 = cta_rank() * blockDim.x; i0 < n; i0 += stride) {
+        for (int i0 = cta_rank() * blockDim.x; i0 < L; i0 += stride) {
             const int i = i0 + (int)threadIdx.x;
-            const int v = v0 + i;
-            bool ok = i < n && ld_claim(v) == kClaimNone;
+            bool ok = i < L;
+            const int v = ok ? ldcg(list + i) : v0;
             const int root = ok ? cc_root((volatile int*)a->cc_parent, v, v0, v0 + n) : -1;
             if (ok && root < 0) {
                 fail_at(kSiteParent, v);

@@ -59,7 +59,7 @@ struct alignas(128) Ctl {
     int pub_lastF;   // size of the last non-empty level when finished
     int comp_count;  // component-table entries left to k_rcm_components (0 = none)
     int comp_nv;     // first label those components may take
-    int pub_pad;
+    int cc_open;     // vertices still unnumbered when the component table is built
     unsigned long long pub_key;    // min (degree, id) key of the last level when finished
     long long pub_reached;         // vertices reached so far (levels-only sweeps)
     long long stats[8];            // rcm_stats fields, in order
