@@ -271,10 +271,14 @@ struct Engine {
     // A row keeps its first kEllNb neighbours in the padded row; the rest (degree > kEllNb) are
     // read from adj. The lanes holding such a row hand it to the whole warp one row at a time, and
     // the warp reads it 32 entries per round, coalesced: a hub of a scale-free graph costs its
-    // degree / 32 rounds instead of its degree serial steps in one thread.
+    // degree / 32 rounds instead of its degree serial steps in one thread. The entries of
+    // kLongRounds rounds are loaded before the first of them is used, so a hub's rounds do not
+    // each wait for their own row read.
     // fn(src, w) runs on all 32 lanes for one round of lane src's row, w = the lane's entry or -1
     // past the row's end; it may use warp-collective operations, and returns true (warp-uniform)
     // to stop reading that row. Must be called by all 32 lanes of the warp.
+    static constexpr int kLongRounds = 4;
+
     template <class Fn>
     __device__ void for_long_rows(bool has, int u, int dg, Fn fn) const {
         unsigned pend = __ballot_sync(0xffffffffu, has && dg > kEllNb);
@@ -285,10 +289,49 @@ struct Engine {
             const int uu = __shfl_sync(0xffffffffu, u, src);
             const int dd = __shfl_sync(0xffffffffu, dg, src);
             const int* row = a->adj + __ldg(a->rowptr + uu);
-            for (int k0 = kEllNb; k0 < dd; k0 += 32) {
-                const int k = k0 + lane;
-                const int w = k < dd ? __ldg(row + k) : -1;
-                if (fn(src, w)) break;
+            for (int k0 = kEllNb; k0 < dd; k0 += 32 * kLongRounds) {
+                int w[kLongRounds];
+#pragma unroll
+                for (int r = 0; r < kLongRounds; ++r) {
+                    const int k = k0 + 32 * r + lane;
+                    w[r] = k < dd ? __ldg(row + k) : -1;
+                }
+                bool stop = false;
+#pragma unroll
+                for (int r = 0; r < kLongRounds; ++r)
+                    if (!stop && k0 + 32 * r < dd) stop = fn(src, w[r]);
+                if (stop) break;
+            }
+        }
+    }
+
+    // The same for the ownership tests of phase B: each round's entries come with their claims,
+    // fn(src, w, claim) (claim = kClaimNone past the row's end), and the entries of kLongRounds
+    // rounds, then their claims, are loaded before any is used: a hub costs two dependent round
+    // trips per kLongRounds rounds, not per round.
+    template <class Fn>
+    __device__ void for_long_rows_claims(bool has, int u, int dg, Fn fn) const {
+        unsigned pend = __ballot_sync(0xffffffffu, has && dg > kEllNb);
+        const int lane = threadIdx.x & 31;
+        while (pend) {
+            const int src = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const int uu = __shfl_sync(0xffffffffu, u, src);
+            const int dd = __shfl_sync(0xffffffffu, dg, src);
+            const int* row = a->adj + __ldg(a->rowptr + uu);
+            for (int k0 = kEllNb; k0 < dd; k0 += 32 * kLongRounds) {
+                int w[kLongRounds];
+                unsigned long long c[kLongRounds];
+#pragma unroll
+                for (int r = 0; r < kLongRounds; ++r) {
+                    const int k = k0 + 32 * r + lane;
+                    w[r] = k < dd ? __ldg(row + k) : -1;
+                }
+#pragma unroll
+                for (int r = 0; r < kLongRounds; ++r) c[r] = w[r] >= 0 ? ld_claim(w[r]) : kClaimNone;
+#pragma unroll
+                for (int r = 0; r < kLongRounds; ++r)
+                    if (k0 + 32 * r < dd) fn(src, w[r], c[r]);
             }
         }
     }
@@ -1399,11 +1442,10 @@ struct Engine {
                     u = -1;
                 }
             }
-            for_long_rows(u >= 0, u, dg, [&](int src, int w) {
+            for_long_rows_claims(u >= 0, u, dg, [&](int src, int w, unsigned long long cw) {
                 const unsigned long long kk = __shfl_sync(0xffffffffu, key, src);
-                const int m = __popc(__ballot_sync(0xffffffffu, w >= 0 && ld_claim(w) == kk));
+                const int m = __popc(__ballot_sync(0xffffffffu, w >= 0 && cw == kk));
                 if ((int)(threadIdx.x & 31) == src) c += m;
-                return false;
             });
             int tot;
             const int ex = cta_scan(c, &tot);
@@ -1466,10 +1508,10 @@ struct Engine {
             }
             // the rest of a long row, in row order: a round's owned entries take consecutive
             // positions after the owner's earlier children
-            for_long_rows(u >= 0, u, dg, [&](int src, int w) {
+            for_long_rows_claims(u >= 0, u, dg, [&](int src, int w, unsigned long long cw) {
                 const int lane = threadIdx.x & 31;
                 const unsigned long long kk = __shfl_sync(0xffffffffu, key, src);
-                const bool own = w >= 0 && ld_claim(w) == kk;
+                const bool own = w >= 0 && cw == kk;
                 const unsigned bal = __ballot_sync(0xffffffffu, own);
                 const int base = __shfl_sync(0xffffffffu, pos, src);
                 if (own) {
@@ -1482,7 +1524,6 @@ struct Engine {
                     }
                 }
                 if (lane == src) pos += __popc(bal);
-                return false;
             });
         }
         __syncthreads();
@@ -1548,11 +1589,10 @@ struct Engine {
             // phase B: the children each vertex owns, counted, then numbered in (key, row) order
             const unsigned mask = u >= 0 ? owned_mask(rw, dg, key) : 0u;
             int cnt = __popc(mask);
-            for_long_rows(u >= 0, u, dg, [&](int src, int w) {
+            for_long_rows_claims(u >= 0, u, dg, [&](int src, int w, unsigned long long cw) {
                 const unsigned long long kk = __shfl_sync(0xffffffffu, key, src);
-                const int m = __popc(__ballot_sync(0xffffffffu, w >= 0 && ld_claim(w) == kk));
+                const int m = __popc(__ballot_sync(0xffffffffu, w >= 0 && cw == kk));
                 if (lane == src) cnt += m;
-                return false;
             });
             const int incl = warp_incl_scan(cnt);
             const int kids = __shfl_sync(0xffffffffu, incl, 31);
@@ -1571,9 +1611,9 @@ struct Engine {
                         ++q;
                     }
             }
-            for_long_rows(u >= 0, u, dg, [&](int src, int w) {
+            for_long_rows_claims(u >= 0, u, dg, [&](int src, int w, unsigned long long cw) {
                 const unsigned long long kk = __shfl_sync(0xffffffffu, key, src);
-                const bool own = w >= 0 && ld_claim(w) == kk;
+                const bool own = w >= 0 && cw == kk;
                 const unsigned bal = __ballot_sync(0xffffffffu, own);
                 const int base = __shfl_sync(0xffffffffu, q, src);
                 if (own) {
@@ -1584,7 +1624,6 @@ struct Engine {
                     if ((unsigned)lab < (unsigned)n) a->perm[n - 1 - lab] = w; else bad = 1;
                 }
                 if (lane == src) q += __popc(bal);
-                return false;
             });
             __syncwarp();
             tick(kPhOwn);
