@@ -67,14 +67,17 @@ const char *rcm_status_string(rcm_status s);
    same permutation. Zero-initialise and set what you need; 0 means "library default" in every field. */
 typedef struct {
     int32_t narrow_threshold;  /* frontier size below which a single CTA runs the levels; -1 = never;
-                                  0 = the CTA width                                                 */
+                                  0 = the CTA width, or 128 on a graph with a vertex of more than
+                                  512 neighbours when fused_sweeps is 0 too (decided on the device) */
     int32_t grid_blocks;       /* CTAs of the persistent grid (<= co-resident limit); 0 = one per SM */
     int32_t block_threads;     /* threads per CTA of the persistent grid: 32 .. 1024 (power of 2); 0 = 512 */
     int32_t fused_sweeps;      /* 1 = label during sweeps 2.. (fused); 2 = label during every sweep,
                                   the first included (its labels are discarded); -1 = levels-only
                                   sweeps, then a separate labelled pass; 0 = 2 on a persistent grid
-                                  of at least 64 CTAs (1 with async_sweeps), 1 on smaller grids,
-                                  clusters and the shared-memory CTA. Same result                  */
+                                  of at least 64 CTAs (1 with async_sweeps, or on a graph with a
+                                  vertex of more than 512 neighbours when narrow_threshold is 0
+                                  too), 1 on smaller grids, clusters and the shared-memory CTA.
+                                  Same result                                                      */
     int64_t spin_limit_ns;     /* bound of every device-side wait; 0 = 20 s                        */
     int64_t nnz;               /* rowptr[n] when the caller knows it: skips the synchronised 4-byte
                                   read (the device still checks it; a mismatch is RCM_ERR_BAD_CSR);

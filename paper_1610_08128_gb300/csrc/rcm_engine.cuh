@@ -52,6 +52,13 @@ constexpr int kEllNb = 7;       // neighbours stored in a vertex's 32-byte row; 
 constexpr int kCache = 2048;    // frontier ids cached in shared memory per buffer
 constexpr int kTinyMax = 32;    // components of at most this many vertices are ordered by one thread
 constexpr int kWarpLevel = 32;  // narrow levels of at most this many vertices run on warp 0 alone
+// A level of a few hundred vertices that holds a hub is far more work than one CTA does quickly,
+// and a labelled first sweep over hubs costs more than a levels-only one: graphs with a vertex of
+// more than kHubDegree neighbours take a lower frontier switch and levels-only first sweeps by
+// default (the 1M-vertex power-law graph with hubs of 7,000: 24.3 ms with the grid defaults,
+// 8.8 ms with these).
+constexpr int kHubDegree = 512;
+constexpr int kHubNarrow = 128;
 constexpr unsigned long long kClaimNone = ~0ull;
 
 struct EngineArgs {
@@ -72,6 +79,9 @@ struct EngineArgs {
     int* diag;                   // optional (may be null): first failed guard's site and value
     int narrow_thr;
     int fused;
+    int hub_auto;                // default launch of the persistent grid: a graph with a vertex of more
+                                 // than kHubDegree neighbours takes the frontier switch kHubNarrow and
+                                 // levels-only first sweeps (decided on the device from ctl->maxdeg)
     int obits;                   // low bits of a key holding the in-level order
     int profile;                 // accumulate per-phase time (CTA 0, thread 0)
     long long limit_ns;

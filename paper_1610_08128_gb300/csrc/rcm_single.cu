@@ -292,6 +292,9 @@ rcm_status single_launch(int n, long long nnz, const rcm_options& o, SingleLaunc
     // 6.8 ms). Asynchronous sweeps are levels-only.
     sl.fused = o.fused_sweeps < 0 ? 0 : o.fused_sweeps == 1 ? 1 : o.fused_sweeps == 2 ? 2
              : (sl.async || sl.blocks < kLabelEverySweepBlocks) ? 1 : 2;
+    // hub graphs (a vertex of more than kHubDegree neighbours) take a lower switch and levels-only
+    // first sweeps, decided on the device, when the caller left both at their defaults
+    sl.hub_auto = o.narrow_threshold == 0 && o.fused_sweeps == 0 && !sl.async ? 1 : 0;
     sl.profile = o.profile_phases ? 1 : 0;
     sl.stall = o.debug_stall_barrier ? 1 : 0;
     sl.l2_persist = o.l2_persist > 0;
@@ -457,6 +460,7 @@ cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* c
     args.obits = sl.obits > 0 ? sl.obits : claim_order_bits(n);
     args.profile = sl.profile;
     args.fused = sl.fused;
+    args.hub_auto = sl.small ? 0 : sl.hub_auto;
     args.limit_ns = sl.limit_ns;
     if (L.cc_cap > 0) {
         args.cc_parent = pool4 + 3 * (size_t)n;

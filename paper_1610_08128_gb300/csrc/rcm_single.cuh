@@ -35,6 +35,7 @@ struct SingleLaunch {
     int narrow = 0;              // frontier size below which CTA 0 runs levels alone
     long long limit_ns = 20000000000LL;
     int fused = 1;               // 0 = separate labelled pass, 1 = labelled sweeps 2.., 2 = every sweep labelled
+    int hub_auto = 0;            // frontier switch and fusing at their defaults: lowered on hub graphs
     int profile = 0;
     int stall = 0;
     bool async = false;          // levels-only sweeps through the asynchronous work queue

@@ -57,6 +57,13 @@ __device__ __forceinline__ void single_run(const EngineArgs& args, int stall, En
     const int n = args.n;
     Engine<false, false, kAsync, kBottomUp> e;
     e.init(args, &smem);
+    if (args.hub_auto && ld_volatile(&ctl->maxdeg) > kHubDegree) {  // the same on every CTA
+        if (threadIdx.x == 0) {
+            smem.args.narrow_thr = min(smem.args.narrow_thr, kHubNarrow);
+            smem.args.fused = 1;
+        }
+        __syncthreads();
+    }
     int Z = 0;
     if (!e.label_isolated(Z)) return;
     e.stat_add(kStIsolated, Z);
