@@ -118,6 +118,13 @@ __device__ __forceinline__ unsigned cluster_rank() {
     return r;
 }
 
+// CTAs in this CTA's cluster (1 for launches without clusters).
+__device__ __forceinline__ unsigned cluster_size() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
 // Hardware barrier of every thread of the cluster (all threads of all its CTAs must arrive).
 __device__ __forceinline__ void cluster_barrier() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");

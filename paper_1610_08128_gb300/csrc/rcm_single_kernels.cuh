@@ -57,6 +57,17 @@ __device__ __forceinline__ void single_run(const EngineArgs& args, int stall, En
     const int n = args.n;
     Engine<false, false, kAsync, kBottomUp> e;
     e.init(args, &smem);
+    // The middle tier reads its peers' shared memory, so it runs only where the launch's clusters
+    // have the shape the host asked for (a profiler that relaunches the kernel may not keep it;
+    // under one, a cluster launch faulted with Xid 13 before this check). Otherwise the levels run
+    // without the tier: the same result. The cluster shape is the same on every CTA.
+    if (args.mid_k > 0 && cluster_size() != (unsigned)args.mid_k) {
+        if (threadIdx.x == 0) {
+            smem.args.mid_k = 0;
+            smem.args.mid_thr = 0;
+        }
+        __syncthreads();
+    }
     if (args.hub_auto && ld_volatile(&ctl->maxdeg) > kHubDegree) {  // the same on every CTA
         if (threadIdx.x == 0) {
             smem.args.narrow_thr = min(smem.args.narrow_thr, kHubNarrow);
