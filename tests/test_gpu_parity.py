@@ -736,6 +736,38 @@ def test_batch_rejects_cross_block_entries():
     assert st == rcm.RCM_ERR_BAD_CSR
 
 
+def test_batch_validation_across_many_small_graphs():
+    """Hundreds of graphs of 0 to 4 vertices, so one warp's 32 rows span many graphs (and empty
+    ones): the valid batch orders as the oracle does, and an entry that leaves its graph's block,
+    forward or backward, anywhere in the batch, is reported."""
+    rcm = rcm_mod()
+    rng = synth.rng_for(191)
+    graphs = []
+    for i in range(400):
+        k = int(rng.integers(0, 5))
+        graphs.append(synth.path(k, seed=[191, i]) if k > 0 else synth.csr_from_edges(0, [], []))
+    b = synth.concat(graphs)
+    goff = torch.from_numpy(b.goff).cuda()
+    rp = torch.from_numpy(b.rowptr).cuda()
+    perm = torch.empty(max(b.n, 1), dtype=torch.int32, device="cuda")
+    rcm.check(rcm.rcm_order_batch(len(graphs), b.n, goff, rp, torch.from_numpy(b.colidx).cuda(), perm), "batch")
+    rcm.check(rcm.rcm_stream_status(), "batch")
+    host = perm.cpu().numpy()
+    for gi, g in enumerate(graphs):
+        assert np.array_equal(host[b.goff[gi]:b.goff[gi + 1]], oracle.rcm(g.n, g.rowptr, g.colidx)), gi
+    big = [gi for gi, g in enumerate(graphs) if g.nnz > 0]
+    for gi, step in ((big[-1], -1), (big[len(big) // 2], 1), (big[len(big) // 3], -1)):
+        colidx = b.colidx.copy()
+        e = int(b.rowptr[b.goff[gi]])
+        colidx[e] = int(b.goff[gi] - 1) if step < 0 else int(b.goff[gi + 1])
+        if not 0 <= colidx[e] < b.n:
+            continue
+        st = rcm.rcm_order_batch(len(graphs), b.n, goff, rp, torch.from_numpy(colidx).cuda(), perm)
+        if st == rcm.RCM_OK:
+            st = rcm.rcm_stream_status()
+        assert st == rcm.RCM_ERR_BAD_CSR, (gi, step)
+
+
 @pytest.mark.slow
 def test_c2_grid192_full_size():
     """The full 192^3 workload in every launch configuration the benchmark's autotuner chooses from
