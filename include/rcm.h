@@ -155,6 +155,13 @@ typedef struct {
                                   otherwise)                                                        */
     int32_t mid_threshold;     /* with mid_cluster: levels below this many vertices (and at least
                                   narrow_threshold) run on the middle tier; 0 = 128 x mid_cluster   */
+    int32_t components_first;  /* persistent grid: 1 = find every component (union-find, Sec. III-B's
+                                  component loop) before the first sweep, instead of sweeping from
+                                  the first start vertex and building the table only when that
+                                  sweep does not reach every vertex. Faster on graphs known to be
+                                  disconnected into components of similar size (that probe sweep is
+                                  serial); one union-find pass more on a connected graph. Same
+                                  result. 0 or -1 = off                                             */
 } rcm_options;
 
 /* Statistics of one ordering (filled by rcm_order_ex when requested). */

@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_rcm_
         a.cc_big = 0;
         a.fused = 1;
         a.hub_auto = 0;
+        a.cc_first = 0;
         a.limit_ns = 0;
         a.fkey = nullptr;  // CTA engines: top-down, level by level
         a.expand_mode = 1;

@@ -184,6 +184,7 @@ static rcm_status check_options(const rcm_options* o) {
         o->mid_cluster != 8 && o->mid_cluster != 16)
         return RCM_ERR_INVALID_ARG;
     if (o->mid_threshold < 0) return RCM_ERR_INVALID_ARG;
+    if (o->components_first < -1 || o->components_first > 1) return RCM_ERR_INVALID_ARG;
     return RCM_OK;
 }
 

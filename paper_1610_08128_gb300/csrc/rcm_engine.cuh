@@ -79,6 +79,7 @@ struct EngineArgs {
     int* diag;                   // optional (may be null): first failed guard's site and value
     int narrow_thr;
     int fused;
+    int cc_first;                // persistent grid: build the component table before the first sweep
     int hub_auto;                // default launch of the persistent grid: a graph with a vertex of more
                                  // than kHubDegree neighbours takes the frontier switch kHubNarrow and
                                  // levels-only first sweeps (decided on the device from ctl->maxdeg)

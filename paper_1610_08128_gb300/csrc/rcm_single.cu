@@ -295,6 +295,7 @@ rcm_status single_launch(int n, long long nnz, const rcm_options& o, SingleLaunc
     // hub graphs (a vertex of more than kHubDegree neighbours) take a lower switch and levels-only
     // first sweeps, decided on the device, when the caller left both at their defaults
     sl.hub_auto = o.narrow_threshold == 0 && o.fused_sweeps == 0 && !sl.async ? 1 : 0;
+    sl.cc_first = o.components_first > 0 ? 1 : 0;
     sl.profile = o.profile_phases ? 1 : 0;
     sl.stall = o.debug_stall_barrier ? 1 : 0;
     sl.l2_persist = o.l2_persist > 0;
@@ -461,6 +462,7 @@ cudaError_t enqueue_single(int n, long long nnz, const int* rowptr, const int* c
     args.profile = sl.profile;
     args.fused = sl.fused;
     args.hub_auto = sl.small ? 0 : sl.hub_auto;
+    args.cc_first = sl.small ? 0 : sl.cc_first;
     args.limit_ns = sl.limit_ns;
     if (L.cc_cap > 0) {
         args.cc_parent = pool4 + 3 * (size_t)n;

@@ -36,6 +36,7 @@ struct SingleLaunch {
     long long limit_ns = 20000000000LL;
     int fused = 1;               // 0 = separate labelled pass, 1 = labelled sweeps 2.., 2 = every sweep labelled
     int hub_auto = 0;            // frontier switch and fusing at their defaults: lowered on hub graphs
+    int cc_first = 0;            // component table before the first sweep
     int profile = 0;
     int stall = 0;
     bool async = false;          // levels-only sweeps through the asynchronous work queue

@@ -81,7 +81,8 @@ __device__ __forceinline__ void single_run(const EngineArgs& args, int stall, En
     e.stat_add(kStComponents, Z);
     int nv = Z;
     int C = -1;
-    bool first = true, tried = false;
+    // with cc_first the component table is built before any sweep (no probe from the first start)
+    bool first = !args.cc_first, tried = false;
     while (nv < n) {
         if (!first && !tried && args.cc_cap > 0) {
             // more than one component: order them concurrently (one attempt)

@@ -49,6 +49,7 @@ class rcm_options(ctypes.Structure):
         ("debug_order_bits", ctypes.c_int32),
         ("mid_cluster", ctypes.c_int32),
         ("mid_threshold", ctypes.c_int32),
+        ("components_first", ctypes.c_int32),
     ]
 
 

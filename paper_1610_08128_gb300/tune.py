@@ -28,6 +28,8 @@ SINGLE_CANDIDATES = [
 ] + [
     {"executor": 1, "narrow_threshold": t, "fused_sweeps": 1} for t in (128, 512)
 ] + [
+    {"executor": 1, "narrow_threshold": 512, "fused_sweeps": 1, "components_first": 1}
+] + [
     {"executor": 1, "expand_mode": 1, "narrow_threshold": 512, "l2_persist": 1, "mid_cluster": k} for k in (8, 16)
 ] + [
     {"executor": 1, "expand_mode": 3, "bottom_up_divisor": dv, "narrow_threshold": t}

@@ -119,7 +119,8 @@ def test_option_checks_come_before_any_device_work(lib):
            ("bottom_up_divisor", -1), ("debug_async_slots", -1), ("executor", 3), ("cluster", 2),
            ("block_threads", 100), ("narrow_threshold", -2), ("grid_blocks", -1), ("spin_limit_ns", -1),
            ("fused_sweeps", 3), ("fused_sweeps", -2), ("l2_persist", 2), ("debug_order_bits", 64),
-           ("debug_order_bits", -1), ("mid_cluster", 3), ("mid_cluster", 32), ("mid_threshold", -1)]
+           ("debug_order_bits", -1), ("mid_cluster", 3), ("mid_cluster", 32), ("mid_threshold", -1),
+           ("components_first", 2), ("components_first", -2)]
     for field, value in bad:
         o = rcm.rcm_options()
         setattr(o, field, value)

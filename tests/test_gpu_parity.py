@@ -381,6 +381,8 @@ OPTION_SETS = [
     {"mid_cluster": 8, "executor": 1, "mid_threshold": 8192},      # a tier far wider than the cluster
     {"mid_cluster": 4, "executor": 1, "mid_threshold": 600},       # a tier of one CTA-0 threshold's width
     {"mid_cluster": 4, "executor": 1, "mid_threshold": 100},       # bound below the CTA-0 threshold: tier unused
+    {"components_first": 1, "executor": 1},                        # component table before any sweep
+    {"components_first": 1, "executor": 1, "narrow_threshold": -1, "fused_sweeps": 2},
 ]
 
 
