@@ -554,7 +554,12 @@ def main():
     from paper_1610_08128_gb300 import synth as synth_mod
 
     workers = synth_mod.default_workers()
-    b.build()
+    # one rank (re)builds the in-tree library while the others wait: concurrent compiles would
+    # write the same objects
+    if rank == 0:
+        b.build()
+    if dist:
+        dist.barrier()
     rcm.load()
     g, cfg = make_workload(args.side)
     n, nnz = g.n, g.nnz
