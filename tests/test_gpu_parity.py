@@ -193,6 +193,21 @@ def test_tiny_components_one_per_thread():
     assert_parity(small, {"executor": 2, "block_threads": 64})
 
 
+def test_warp_levels_expanding_past_the_frontier_cache():
+    """A one-vertex level whose hub expands to more vertices than the shared frontier cache holds
+    (2,048): the warp-0 run hands over a level kept in global memory. On the shared-memory CTA (a
+    star of 3,000 leaves alone) and in the component kernel (the same star beside a grid)."""
+    star = synth.csr_from_edges(3001, np.zeros(3000, np.int64), np.arange(1, 3001))
+    g = synth.permute(star, synth.random_permutation(star.n, 201))
+    assert_parity(g, {"executor": 2, "block_threads": 64})
+    assert_parity(g, {"executor": 2, "block_threads": 256})
+    b = synth.concat([star, synth.grid((60, 60), seed=202)])
+    mixed = synth.permute(synth.Csr(b.n, b.rowptr, b.colidx), synth.random_permutation(b.n, 203))
+    assert_parity(mixed)
+    assert_parity(mixed, {"executor": 1, "components_first": 1})
+    assert_parity(mixed, {"executor": 1, "fused_sweeps": -1})
+
+
 def test_tiny_components_in_the_batch():
     """The batched engine orders each graph's tiny components one per thread."""
     rcm = rcm_mod()
