@@ -387,6 +387,59 @@ def test_alg3_level_form_equals_queue_form():
         assert np.array_equal(perm, rcm_of(g))
 
 
+def test_fifo_traversal_over_sorted_rows_is_the_ordering_of_each_component():
+    """The one-thread ordering of tiny components rests on this: with every row stored in (degree,
+    id) order, a plain FIFO traversal that appends each dequeued vertex's unvisited neighbours in
+    row order numbers a component as Alg. 1 does, and its level boundaries give Alg. 2 the
+    eccentricity and the last level's least (degree, id) vertex. Restated per component (sweeps
+    from the component's start vertex while the eccentricity grows strictly, the last root's
+    traversal as its numbering; components in start order; one reversal) and compared with the
+    oracle, sweep counts included, on small graphs of many components."""
+    graphs = small_graphs(150, 60, 31) + small_graphs(40, 300, 32)
+    for g in graphs:
+        deg = oracle.degrees(g.n, g.rowptr, g.colidx).astype(np.int64)
+        rows = []
+        for v in range(g.n):
+            nb = [int(w) for w in g.colidx[g.rowptr[v]:g.rowptr[v + 1]] if w != v]
+            rows.append(sorted(nb, key=lambda w: (deg[w], w)))
+
+        def fifo(root):
+            seen = {root}
+            q = [root]
+            head, lend, ecc, lmin = 0, 1, 0, None
+            while True:
+                u = q[head]
+                head += 1
+                key = (int(deg[u]), u)
+                lmin = key if lmin is None or key < lmin else lmin
+                for w in rows[u]:
+                    if w not in seen:
+                        seen.add(w)
+                        q.append(w)
+                if head == lend:
+                    if len(q) == lend:
+                        return ecc, lmin[1], q
+                    ecc, lend, lmin = ecc + 1, len(q), None
+
+        labelled, seq, sweeps = set(), [], 0
+        for r0 in sorted(range(g.n), key=lambda v: (deg[v], v)):
+            if r0 in labelled:
+                continue
+            ecc_prev, r, q = fifo(r0)
+            sweeps += 1
+            while True:
+                ecc, nxt, q = fifo(r)
+                sweeps += 1
+                if ecc <= ecc_prev:
+                    break
+                ecc_prev, r = ecc, nxt
+            seq += q
+            labelled.update(q)
+        want, st = oracle.rcm(g.n, g.rowptr, g.colidx, with_stats=True)
+        assert np.array_equal(np.array(seq[::-1], dtype=np.int64), want.astype(np.int64))
+        assert sweeps == st["sweeps"]
+
+
 def test_sort_free_variant_level_form_equals_queue_form():
     """The sort-free variant (children in stored row order) against the level form with the key
     (parent label, position in the parent's row)."""
