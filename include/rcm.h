@@ -210,7 +210,8 @@ rcm_status rcm_order_ex(int32_t n, const int32_t *rowptr, const int32_t *colidx,
 /*
  * rcm_order_host -- end-to-end ordering from host memory: copies the pattern to the device,
  * orders it on `stream`, copies perm back, and synchronises. Returns the final status
- * (device-detected errors included).
+ * (device-detected errors included). On the persistent grid it uses the L2 window of
+ * rcm_options.l2_persist (the call synchronises anyway; same result).
  *   rowptr host int32[n+1], colidx host int32[rowptr[n]], perm_out host int32[n].
  * Pinned (page-locked) host buffers give the fastest copies; pageable ones work.
  */

@@ -294,7 +294,11 @@ rcm_status rcm_order_host(int32_t n, const int32_t* rowptr, const int32_t* colid
     cudaError_t e = cudaMemcpyAsync(d_rp, rowptr, sizeof(int) * ((size_t)n + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && nnz > 0)
         e = cudaMemcpyAsync(d_ci, colidx, sizeof(int) * (size_t)nnz, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) st = order_single(n, nnz, d_rp, d_ci, d_pm, nullptr, nullptr, nullptr, s);
+    // the L2 window on the persistent grid (rcm_options.l2_persist): this call synchronises
+    // anyway, which is the window's only cost (the 192^3 grid: 6.8 against 7.1 ms)
+    rcm_options o{};
+    o.l2_persist = 1;
+    if (e == cudaSuccess) st = order_single(n, nnz, d_rp, d_ci, d_pm, &o, nullptr, nullptr, s);
     if (e == cudaSuccess && st == RCM_OK)
         e = cudaMemcpyAsync(perm_out, d_pm, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost, s);
     ws_free(buf, s);
