@@ -380,9 +380,9 @@ def bench_batched(args, torch, rcm, synth, workers, rank=0, world=1, dist=None):
             "sample_equal_to_plain": bool(same), "tuned": best,
             "tuning_ms": {",".join(f"{k}={v}" for k, v in c.items()): round(ms, 3) for c, ms in table},
             "launch": "CUDA graph replay of the batch's launches",
-            # per replay: k_batch_validate, k_degree_validate, k_sort_rows_small, k_sort_rows_big, k_rcm_batch
-            # (the plan's status is read with a copy, not a kernel)
-            "gpu_launches": 5}
+            # per replay: k_degree_validate (with the blocks' check), k_sort_rows_small, k_sort_rows_big,
+            # k_rcm_batch (the plan's status is read with a copy, not a kernel)
+            "gpu_launches": 4}
 
 
 def served_setup(args, torch, rcm, synth, workers):

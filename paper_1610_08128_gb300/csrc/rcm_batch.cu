@@ -15,34 +15,6 @@
 
 namespace rcm {
 
-// Every stored entry of graph g's rows must stay inside graph g's block, and goff must be a
-// non-decreasing offset array ending at n_total.
-__global__ void k_batch_validate(int G, int n_total, const long long* __restrict__ goff,
-                                 const int* __restrict__ rowptr, const int* __restrict__ colidx, Ctl* ctl) {
-    if (blockIdx.x == 0 && threadIdx.x == 0 && (goff[0] != 0 || goff[G] != n_total)) atomicOr(&ctl->status, kErrBadCsr);
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x)
-        if (goff[g + 1] < goff[g]) atomicOr(&ctl->status, kErrBadCsr);
-    if (ld_volatile(&ctl->status) & kErrBadCsr) return;
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n_total; v += gridDim.x * blockDim.x) {
-        // graph of row v: the last g with goff[g] <= v
-        int lo = 0, hi = G - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (goff[mid] <= v) lo = mid; else hi = mid - 1;
-        }
-        const long long a = goff[lo], b = goff[lo + 1];
-        const int r0 = rowptr[v], r1 = rowptr[v + 1];
-        if (r0 < 0 || r1 < r0 || r1 > rowptr[n_total]) {
-            atomicOr(&ctl->status, kErrBadCsr);
-            continue;
-        }
-        for (int k = r0; k < r1; ++k) {
-            const int w = colidx[k];
-            if (w < a || w >= b) atomicOr(&ctl->status, kErrBadCsr);
-        }
-    }
-}
-
 constexpr int kBatchSortCap = 2048;  // component tables sorted in shared memory up to this size
 
 // CTAs per SM the batched executor is compiled for: many graphs are small, so occupancy matters
@@ -223,8 +195,9 @@ cudaError_t enqueue_batch(int G, long long n_total, int nnz, const long long* go
     const int pgrid = (int)std::max<long long>(1, std::min<long long>((n_total + pb - 1) / pb, (long long)di.sms * 16));
     // rows longer than small_max entries number at most nnz / (small_max + 1)
     const int big_grid = (int)std::max<long long>(1, std::min<long long>(3LL * di.sms, nnz / (t.small_max + 1)));
-    if (G > 1) k_batch_validate<<<pgrid, pb, 0, s>>>(G, (int)n_total, goff, rowptr, colidx, ctl);
-    k_degree_validate<<<pgrid, pb, 0, s>>>((int)n_total, nnz, rowptr, colidx, deg, claim, vis, big, ctl, t.small_max);
+    // one pass over the entries checks the structure and each graph's block (G > 1) and counts degrees
+    k_degree_validate<<<pgrid, pb, 0, s>>>((int)n_total, nnz, rowptr, colidx, deg, claim, vis, big, ctl, t.small_max,
+                                           nullptr, nullptr, G > 1 ? goff : nullptr, G);
     k_sort_rows_small<<<pgrid, pb, 0, s>>>((int)n_total, rowptr, colidx, deg, adj, ell, ctl, t.small_max,
                                            t.by_degree);
     k_sort_rows_big<<<big_grid, kBigRowThreads, sizeof(unsigned long long) * kBigRowSmem, s>>>(

@@ -17,14 +17,45 @@ namespace rcm {
 __global__ void k_degree_validate(int n, int nnz, const int* __restrict__ rowptr, const int* __restrict__ colidx,
                                   int* __restrict__ deg, unsigned long long* __restrict__ claim, int* __restrict__ vis,
                                   int* __restrict__ bigrows, Ctl* ctl, int small_max,
-                                  unsigned long long* __restrict__ adist, unsigned long long* __restrict__ fkey) {
+                                  unsigned long long* __restrict__ adist, unsigned long long* __restrict__ fkey,
+                                  const long long* __restrict__ goff, int G) {
     __shared__ int s_max;
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0 && (rowptr[0] != 0 || rowptr[n] != nnz || nnz < 0))
         atomicOr(&ctl->status, kErrBadCsr);
+    const int stride = gridDim.x * blockDim.x;
+    if (goff) {  // a batch: goff must be non-decreasing from 0 to n
+        if (blockIdx.x == 0 && threadIdx.x == 0 && (goff[0] != 0 || goff[G] != n)) atomicOr(&ctl->status, kErrBadCsr);
+        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += stride)
+            if (goff[g + 1] < goff[g]) atomicOr(&ctl->status, kErrBadCsr);
+    }
+    // A warp takes 32 consecutive rows. In a batch, every entry of a row must stay inside its
+    // graph's block [goff[g], goff[g+1]): lane 0 finds the graph of the warp's first row (binary
+    // search) and every lane steps forward from there to its own.
+    const int lane = threadIdx.x & 31;
     int local_max = 0;
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    for (int v0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); v0 < n; v0 += stride) {
+        const int v = v0 + lane;
+        long long lo = 0, hi = n;
+        if (goff) {
+            int g = 0;
+            if (lane == 0) {
+                int l = 0, h = G - 1;
+                while (l < h) {
+                    const int mid = (l + h + 1) >> 1;
+                    if (goff[mid] <= v0) l = mid; else h = mid - 1;
+                }
+                g = l;
+            }
+            g = __shfl_sync(0xffffffffu, g, 0);
+            if (v < n) {
+                while (g + 1 < G && goff[g + 1] <= v) ++g;
+                lo = goff[g];
+                hi = goff[g + 1];
+            }
+        }
+        if (v >= n) continue;
         const int a = rowptr[v], b = rowptr[v + 1];
         int d = 0;
         if (a < 0 || b < a || b > nnz) {
@@ -32,7 +63,7 @@ __global__ void k_degree_validate(int n, int nnz, const int* __restrict__ rowptr
         } else {
             for (int k = a; k < b; ++k) {
                 const int w = colidx[k];
-                if ((unsigned)w >= (unsigned)n) {
+                if ((unsigned)w >= (unsigned)n || w < lo || w >= hi) {
                     atomicOr(&ctl->status, kErrBadCsr);
                 } else if (w != v) {
                     ++d;

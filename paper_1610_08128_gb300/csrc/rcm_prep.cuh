@@ -157,12 +157,14 @@ __device__ __forceinline__ void sort_small_row(int v, const int* __restrict__ ro
 
 // nnz: the stored-entry count the caller sized its buffers for; rowptr[n] must equal it, and no
 // row is read beyond it. adist, fkey (may be null): the asynchronous sweeps' per-vertex words
-// (set to ~0) and the bottom-up frontier keys (set to 0).
+// (set to ~0) and the bottom-up frontier keys (set to 0). goff (may be null): a batch of G graphs
+// stacked block-diagonally; every row's entries must then stay inside its graph's block.
 __global__ void k_degree_validate(int n, int nnz, const int* __restrict__ rowptr, const int* __restrict__ colidx,
                                   int* __restrict__ deg, unsigned long long* __restrict__ claim, int* __restrict__ vis,
                                   int* __restrict__ bigrows, Ctl* ctl, int small_max,
                                   unsigned long long* __restrict__ adist = nullptr,
-                                  unsigned long long* __restrict__ fkey = nullptr);
+                                  unsigned long long* __restrict__ fkey = nullptr,
+                                  const long long* __restrict__ goff = nullptr, int G = 0);
 
 // small_max (<= kSmallRowMax): rows with at most this many stored entries are sorted here, one
 // thread per row; k_degree_validate lists the longer ones for k_sort_rows_big with the same value.
